@@ -1,0 +1,402 @@
+"""Pins for the FP64 CPU oracle: checks against facts fixed by the paper and by
+mathematics, not against the oracle itself.
+
+  * Philox4x32-10 against the published known-answer vectors;
+  * App. A: Green's function of the ball (normalisation by its flux, zero on
+    the sphere, harmonic away from the centre) and its printed integrals;
+  * Sec. 4.6 source sampling against the radial CDF of the normalised G_B
+    (obtained by quadrature of G_B, not by retyping the sampler);
+  * Q.1-Q.3 on tiny shapes with hand-derived answers;
+  * Q.4 (Algs. 5-6): E[1{|z-x|<r}/pdf] equals the measure of the Neumann
+    boundary inside the ball;
+  * the walk: exact harmonic and Poisson solutions, the Poisson kernel of the
+    disk (pure Dirichlet = walk on spheres), mixed Dirichlet/Neumann problems
+    in 2D and 3D, 1/sqrt(N) convergence, and per-step invariants.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle
+from statcheck import check_z
+from paper_2302_11815_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# random numbers
+# ---------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            lhs, rhs = line.split(":")
+            w = [int(t, 16) for t in lhs.split()]
+            want = [int(t, 16) for t in rhs.split()]
+            got = oracle.philox(w[:4], w[4:6])
+            assert [int(v) for v in got] == want
+            rows += 1
+    assert rows == 3
+
+
+# ---------------------------------------------------------------------------
+# App. A: Green's function of the ball
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_green_ball_is_the_dirichlet_green_function(dim):
+    R = 0.7
+    G = lambda rho: oracle.green_ball(dim, rho, R)
+    # vanishes on the sphere
+    assert abs(G(R)) < 1e-15
+    # unit flux of -grad G through every sphere around the pole (delta source)
+    area = (lambda rho: 2 * math.pi * rho) if dim == 2 else (lambda rho: 4 * math.pi * rho**2)
+    for rho in (0.05, 0.3, 0.6):
+        h = 1e-6 * rho
+        dG = (G(rho + h) - G(rho - h)) / (2 * h)
+        assert abs(-dG * area(rho) - 1.0) < 1e-6
+    # harmonic away from the pole: radial Laplacian by finite differences
+    for rho in (0.1, 0.4):
+        h = 1e-4
+        d2 = (G(rho + h) - 2 * G(rho) + G(rho - h)) / h**2
+        d1 = (G(rho + h) - G(rho - h)) / (2 * h)
+        assert abs(d2 + (dim - 1) / rho * d1) < 1e-4 * abs(d2)
+
+
+def test_green_ball_integrals_match_app_a():
+    want = {}
+    with open(os.path.join(GOLDEN, "green_ball_app_a.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            d, c = line.split()
+            want[int(d)] = float(c)
+    for dim in (2, 3):
+        for R in (0.25, 1.0, 3.0):
+            shell = (lambda rho: 2 * math.pi * rho) if dim == 2 else (lambda rho: 4 * math.pi * rho**2)
+            quad, _ = integrate.quad(lambda rho: oracle.green_ball(dim, rho, R) * shell(rho), 0, R,
+                                     limit=200)
+            assert abs(quad - want[dim] * R * R) < 1e-9 * R * R
+            assert abs(oracle.green_ball_norm(dim, R) - want[dim] * R * R) < 1e-14 * R * R
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_source_radius_follows_normalised_green_function(dim):
+    """Sec. 4.6: t ~ G_B(x, x + t v) along v.  The CDF of t/R is obtained
+    here by quadrature of G_B times the shell measure."""
+    R = 1.0
+    shell = (lambda rho: rho) if dim == 2 else (lambda rho: rho**2)
+    norm, _ = integrate.quad(lambda s: oracle.green_ball(dim, s, R) * shell(s), 0, R)
+    grid = np.linspace(1e-9, 1.0, 2001)
+    cdf_vals = np.array([integrate.quad(lambda s: oracle.green_ball(dim, s, R) * shell(s), 0, g)[0]
+                         for g in grid]) / norm
+    rng = np.random.default_rng(5)
+    u = rng.random((20000, 2))
+    t = np.array([oracle.source_radius(dim, R, a, b) for a, b in u])
+    assert np.all((t > 0) & (t < R))
+    res = stats.kstest(t, lambda q: np.interp(q, grid, cdf_vals))
+    assert res.pvalue > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# queries on tiny shapes
+# ---------------------------------------------------------------------------
+def _scene(dim, V, P, flags):
+    return oracle.Scene({"dim": dim, "vertices": np.array(V, float), "prims": np.array(P, np.int32),
+                         "flags": np.array(flags, np.uint8),
+                         "g": {"kind": "analytic", "fn": "zero"}, "h": {"kind": "analytic", "fn": "zero"},
+                         "f": {"kind": "none"}})
+
+
+def test_q1_closest_point_2d_square():
+    S = _scene(2, [[0, 0], [1, 0], [1, 1], [0, 1]], [[0, 1], [1, 2], [2, 3], [3, 0]], [0, 0, 0, 0])
+    d, xb, pr = oracle.closest_dirichlet(S, [[0.3, 0.2], [0.9, 0.5], [2.0, 2.0], [-1.0, 0.5]])
+    np.testing.assert_allclose(d, [0.2, 0.1, math.sqrt(2), 1.0], atol=1e-14)
+    np.testing.assert_allclose(xb, [[0.3, 0], [1, 0.5], [1, 1], [0, 0.5]], atol=1e-14)
+    assert list(pr[[0, 1, 3]]) == [0, 1, 3]
+
+
+def test_q1_closest_point_3d_triangle_regions():
+    S = _scene(3, [[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 2]], [0])
+    q = [[0.2, 0.2, 0.5], [-1, -1, 0], [0.5, -1, 0], [1, 1, 0], [0.1, 0.1, -2]]
+    d, xb, _ = oracle.closest_dirichlet(S, q)
+    np.testing.assert_allclose(d, [0.5, math.sqrt(2), 1.0, math.sqrt(0.5), 2.0], atol=1e-14)
+    np.testing.assert_allclose(xb[3], [0.5, 0.5, 0], atol=1e-14)
+
+
+def test_q2_convex_neumann_polygon_has_no_silhouette_from_inside():
+    # Sec. 4.4 / Sec. 5.1: from inside a convex region the Neumann boundary is
+    # never a visibility silhouette, so d_sil = r_max
+    V = scenes.regular_polygon(64)
+    P = scenes.closed_polyline(V)
+    S = _scene(2, V, P, np.ones(64))
+    rng = np.random.default_rng(1)
+    pts = scenes.ball_points(rng, 200, 2, 0.9)
+    d, w = oracle.silhouette_distance(S, pts, 10.0)
+    assert np.all(d == 10.0) and np.all(w == -1)
+
+
+def test_q2_reflex_vertex_is_the_silhouette():
+    # L-shaped room (all Neumann).  Seen from inside an arm, the reflex
+    # corner (1,1) is the only silhouette point: one of its walls faces the
+    # viewer and the other turns away.  From the square where the arms
+    # overlap both walls face the viewer: no silhouette.
+    V = [[0, 0], [2, 0], [2, 1], [1, 1], [1, 2], [0, 2]]
+    P = scenes.closed_polyline(np.array(V, float))
+    S = _scene(2, V, P, np.ones(6))
+    q = np.array([[0.5, 1.5], [1.5, 0.5], [0.3, 0.4]])
+    d, w = oracle.silhouette_distance(S, q, 100.0)
+    want = np.linalg.norm(q - np.array([1.0, 1.0]), axis=1)
+    want[2] = 100.0
+    np.testing.assert_allclose(d, want, atol=1e-14)
+    assert list(w[:2]) == [3, 3] and w[2] == -1
+
+
+def test_q2_straight_wall_independent_of_subdivision():
+    # Sec. 1: steps are independent of the tessellation; interior vertices of
+    # a straight wall are never silhouettes, its two ends always are
+    rng = np.random.default_rng(2)
+    q = np.c_[rng.uniform(-2, 2, 100), rng.uniform(0.05, 1.5, 100)]
+    ref = None
+    for k in (1, 3, 16, 101):
+        xs = np.linspace(-1, 1, k + 1)
+        V = np.c_[xs, np.zeros(k + 1)]
+        P = np.c_[np.arange(k), np.arange(1, k + 1)]
+        S = _scene(2, V, P, np.ones(k))
+        d, _ = oracle.silhouette_distance(S, q, 100.0)
+        want = np.minimum(np.linalg.norm(q - [-1, 0], axis=1), np.linalg.norm(q - [1, 0], axis=1))
+        np.testing.assert_allclose(d, want, atol=1e-13)
+        ref = d if ref is None else ref
+        np.testing.assert_allclose(d, ref, atol=1e-13)
+
+
+def test_q2_3d_closed_cube_from_inside_and_open_triangle():
+    V, P = scenes.cube_mesh(3)
+    S = _scene(3, V, P, np.ones(len(P)))
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-0.9, 0.9, (100, 3))
+    d, _ = oracle.silhouette_distance(S, pts, 7.0)
+    assert np.all(d == 7.0)
+    # a lone triangle: all three edges are boundary edges, hence silhouettes
+    T = _scene(3, [[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 2]], [1])
+    d, _ = oracle.silhouette_distance(T, [[0.2, 0.2, 0.3], [0.25, -0.5, 0.0]], 10.0)
+    np.testing.assert_allclose(d, [math.sqrt(0.2**2 + 0.3**2), 0.5], atol=1e-14)
+
+
+def test_q2_3d_sphere_silhouette_is_the_tangent_circle():
+    V, P = scenes.sphere_mesh(48, 96, 1.0)
+    S = _scene(3, V, P, np.ones(len(P)))
+    for D in (1.5, 2.0, 4.0):
+        d, _ = oracle.silhouette_distance(S, [[0.0, 0.3 * D, math.sqrt(1 - 0.09) * D]], 100.0)
+        # within the angular resolution of the inscribed mesh (pi/48)
+        assert abs(d[0] - math.sqrt(D * D - 1)) < 0.06 and d[0] > D - 1
+
+
+def test_q3_ray_hits_2d_and_3d():
+    S = _scene(2, [[0, 0], [1, 0], [1, 1], [0, 1]], [[0, 1], [1, 2], [2, 3], [3, 0]], [1, 1, 1, 0])
+    hit, t, pr = oracle.intersect_neumann(S, [[0.5, 0.5], [0.5, 0.5], [0.5, 0.5]],
+                                          [[0, -1], [1, 0], [-1, 0]], [1.0, 0.4, 1.0])
+    assert list(hit) == [True, False, False]  # the left wall is Dirichlet
+    assert abs(t[0] - 0.5) < 1e-15 and pr[0] == 0
+    T = _scene(3, [[0, 0, 0], [1, 0, 0], [0, 1, 0]], [[0, 1, 2]], [1])
+    hit, t, _ = oracle.intersect_neumann(T, [[0.2, 0.2, 1.0]] * 4,
+                                         [[0, 0, -1], [0, 0, -1], [0, 0, 1], [0, 0, -1]],
+                                         [2.0, 0.5, 2.0, 2.0], skip=[-1, -1, -1, 0])
+    assert list(hit) == [True, False, False, False]
+    assert abs(t[0] - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Q.4: hierarchical Neumann sampling (Algs. 5-6) is unbiased
+# ---------------------------------------------------------------------------
+def _sample_measure(S, x, r, n, seed):
+    vals = np.zeros(n)
+    for i in range(n):
+        z, _, pdf, pr = oracle.neumann_sample(S, x, r, seed, i, 0, 0)
+        if pr >= 0 and pdf > 0 and np.linalg.norm(z - np.asarray(x)) < r:
+            vals[i] = 1.0 / pdf
+    return vals
+
+
+def test_q4_measure_of_wall_in_ball_2d():
+    k = 200
+    xs = np.linspace(-2, 2, k + 1)
+    S = _scene(2, np.c_[xs, 0.05 * np.sin(0 * xs)], np.c_[np.arange(k), np.arange(1, k + 1)], np.ones(k))
+    x, r = [0.1, 0.3], 0.5
+    vals = _sample_measure(S, x, r, 20000, 11)
+    want = 2 * math.sqrt(r * r - 0.3**2)
+    assert abs(vals.mean() - want) < 4 * vals.std() / math.sqrt(len(vals))
+    # ball covering the whole boundary: E[1/pdf] = total length
+    vals = _sample_measure(S, [0.0, 0.5], 10.0, 4000, 12)
+    assert abs(vals.mean() - 4.0) < 1e-9 * 4 + 4 * vals.std() / math.sqrt(len(vals))
+
+
+def test_q4_measure_of_plate_in_ball_3d():
+    m = 24
+    g = np.linspace(-1, 1, m + 1)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    V = np.c_[A.ravel(), B.ravel(), np.zeros(A.size)]
+    idx = np.arange((m + 1) ** 2).reshape(m + 1, m + 1)
+    a, b, c, d = idx[:-1, :-1].ravel(), idx[1:, :-1].ravel(), idx[1:, 1:].ravel(), idx[:-1, 1:].ravel()
+    P = np.concatenate([np.c_[a, b, c], np.c_[a, c, d]])
+    S = _scene(3, V, P, np.ones(len(P)))
+    x, r = [0.1, -0.2, 0.3], 0.5
+    vals = _sample_measure(S, x, r, 20000, 13)
+    want = math.pi * (r * r - 0.09)
+    assert abs(vals.mean() - want) < 4 * vals.std() / math.sqrt(len(vals))
+
+
+# ---------------------------------------------------------------------------
+# the walk (Alg. 1) against exact solutions
+# ---------------------------------------------------------------------------
+def _check_exact(sc, pts, walks, eps, seed=7, z=4.0, r_min=None, chi2=True):
+    S = oracle.Scene(sc)
+    res = oracle.solve(S, pts, walks, eps, r_min, 1024, seed=seed)
+    fn, pr = sc["exact"]
+    u = scenes.exact_u(fn, pr, pts)
+    # epsilon-shell bias bound: |u(xbar) - u(x)| <= eps * max|grad u|
+    L = np.max(np.linalg.norm(scenes.exact_grad(fn, pr, sc["vertices"].astype(float)), axis=1))
+    allow = eps * 1.05 * L
+    err = res["mean"] - u
+    assert res["capped"].sum() == 0
+    check_z(err, res["se"], allow, zthr=z, band=(0.5, 1.8) if chi2 else None)
+    return res, u
+
+
+def test_walk_pure_dirichlet_harmonic_disk():
+    # pure Dirichlet: WoSt reduces to walk on spheres (Sec. 3.4, Sec. 4.3)
+    rng = np.random.default_rng(21)
+    pts = scenes.ball_points(rng, 64, 2, 0.9)
+    _check_exact(scenes.disk_scene(256, "exp_cos"), pts, 1024, 1e-3)
+
+
+def test_walk_poisson_kernel_of_the_disk():
+    """Dirichlet data = indicator of the arc [0, pi/2] on the unit circle:
+    u(x) is the harmonic measure, the integral of the disk's Poisson kernel
+    (1 - |x|^2) / (2 pi |x - z|^2) over the arc."""
+    n = 1024
+    sc = scenes.disk_scene(n, "zero")
+    ind = (np.arange(n) < n // 4).astype(np.float32)
+    sc["g"] = {"kind": "per_corner", "values": np.c_[ind, ind]}
+    S = oracle.Scene(sc)
+    rng = np.random.default_rng(22)
+    pts = scenes.ball_points(rng, 48, 2, 0.85)
+    res = oracle.solve(S, pts, 2048, 1e-4, None, 1024, seed=3)
+
+    def hm(x):
+        f = lambda th: (1 - x @ x) / (2 * np.pi * ((x[0] - np.cos(th)) ** 2 + (x[1] - np.sin(th)) ** 2))
+        return integrate.quad(f, 0, np.pi / 2, limit=200)[0]
+
+    want = np.array([hm(p.astype(float)) for p in pts])
+    check_z(res["mean"] - want, res["se"], 0.0)
+    # the centre sees a quarter of the circle
+    c = oracle.solve(S, np.zeros((1, 2)), 8192, 1e-4, None, 1024, seed=4)
+    assert abs(c["mean"][0] - 0.25) < 4 * c["se"][0]
+
+
+def test_walk_source_term_sign_and_norm_2d_3d():
+    # -Lap u = 1 with u = (1 - |x|^2)/(2 dim): pins the sign of S and |G_B|
+    rng = np.random.default_rng(23)
+    _check_exact(scenes.disk_scene(256, "bump", source=True), scenes.ball_points(rng, 48, 2, 0.9), 1024, 1e-3)
+    _check_exact(scenes.cube_scene(4, "bump", source=True), rng.uniform(-0.8, 0.8, (32, 3)), 512, 1e-3)
+
+
+def test_walk_mixed_flower_exp_cos():
+    # the 64-segment flower with alternating Dirichlet/Neumann segments and
+    # u = e^x cos y: pins the sign of the Neumann term, alpha and the hemisphere
+    sc = scenes.config1()
+    res, u = _check_exact(sc, sc["points"], 512, 1e-3)
+    rel = np.sqrt(np.mean((res["mean"] - u) ** 2) / np.mean(u**2))
+    assert rel < 0.05
+
+
+def test_walk_mixed_square_and_annulus():
+    rng = np.random.default_rng(24)
+    pts = (0.05 + 0.9 * rng.random((48, 2))).astype(np.float32)
+    _check_exact(scenes.square_scene(8), pts, 1024, 1e-3)  # u = y, Neumann top/bottom
+    ann = scenes.annulus_scene()
+    r = np.sqrt(rng.uniform(0.35**2, 0.95**2, 48))
+    th = rng.uniform(0, 2 * np.pi, 48)
+    _check_exact(ann, np.c_[r * np.cos(th), r * np.sin(th)].astype(np.float32), 1024, 1e-3)
+
+
+def test_walk_3d_cube_around_neumann_sphere():
+    sc = scenes.box_sphere_scene()
+    rng = np.random.default_rng(25)
+    p = rng.uniform(-0.9, 0.9, (200, 3))
+    p = p[np.linalg.norm(p, axis=1) > 0.5][:32].astype(np.float32)
+    _check_exact(sc, p, 512, 1e-3)
+
+
+def test_walk_3d_pure_dirichlet_cube_quad():
+    rng = np.random.default_rng(26)
+    _check_exact(scenes.cube_scene(4, "quad3"), rng.uniform(-0.9, 0.9, (32, 3)).astype(np.float32), 512, 1e-3)
+
+
+def test_walk_rmse_converges_as_one_over_sqrt_n():
+    # Sec. 6.2: error of magnitude O(1/sqrt(N))
+    sc = scenes.disk_scene(256, "exp_cos", neumann=(np.arange(256) < 64).astype(np.uint8))
+    S = oracle.Scene(sc)
+    rng = np.random.default_rng(27)
+    pts = scenes.ball_points(rng, 64, 2, 0.8)
+    u = scenes.exact_u("exp_cos", (), pts)
+    Ns = [16, 64, 256, 1024]
+    rmse = []
+    for i, N in enumerate(Ns):
+        res = oracle.solve(S, pts, N, 1e-4, None, 1024, seed=100 + i)
+        rmse.append(np.sqrt(np.mean((res["mean"] - u) ** 2)))
+    slope = np.polyfit(np.log(Ns), np.log(rmse), 1)[0]
+    assert -0.65 < slope < -0.35, slope
+
+
+# ---------------------------------------------------------------------------
+# per-step invariants of the walk
+# ---------------------------------------------------------------------------
+def _silhouette_vertices_2d(sc):
+    V = sc["vertices"].astype(float)
+    n = scenes.prim_normals(sc)
+    adj = {}
+    for p in np.nonzero(sc["flags"])[0]:
+        for k in range(2):
+            adj.setdefault(int(sc["prims"][p, k]), []).append(n[p])
+    return V, adj
+
+
+@pytest.mark.parametrize("which", ["flower", "koch"])
+def test_walk_step_invariants(which):
+    sc = scenes.config1() if which == "flower" else scenes.config2(grid=24, level=3)
+    eps = sc["epsilon"]
+    S = oracle.Scene(sc)
+    V, adj = _silhouette_vertices_2d(sc)
+    Nseg = np.nonzero(sc["flags"])[0]
+    A = V[sc["prims"][Nseg, 0]]
+    B = V[sc["prims"][Nseg, 1]]
+    checked = 0
+    npts, nw = (40, 4) if which == "flower" else (12, 2)
+    for i, x0 in enumerate(sc["points"][:npts]):
+        for j in range(nw):
+            val, rows, capped = oracle.walk_trace(S, x0, i, j, eps, sc["r_min"], sc["max_steps"], seed=9)
+            assert not capped and np.isfinite(val)
+            for k in range(len(rows) - 1):
+                x, onN, dD, dsil, r, hit, tb = rows[k, [0, 1]], rows[k, 3], rows[k, 4], rows[k, 5], rows[k, 6], rows[k, 7], rows[k, 8]
+                assert dD >= eps and r <= dD and r >= min(sc["r_min"], dD) - 1e-15
+                xn = rows[k + 1, [0, 1]]
+                assert np.linalg.norm(xn - x) <= r * (1 + 1e-9) + 1e-9
+                if rows[k + 1, 3]:  # next point lies on the Neumann boundary
+                    e = B - A
+                    t = np.clip(np.sum((xn - A) * e, 1) / np.sum(e * e, 1), 0, 1)
+                    assert np.min(np.linalg.norm(A + t[:, None] * e - xn, axis=1)) < 1e-9
+                if not onN and r > sc["r_min"] * (1 + 1e-12):
+                    # no visibility-silhouette vertex strictly inside the star ball
+                    for vid, ns in adj.items():
+                        v = V[vid] - x
+                        dv = np.linalg.norm(v)
+                        if dv < r * (1 - 1e-12):
+                            assert len(ns) == 2 and (v @ ns[0]) * (v @ ns[1]) > 0
+                    checked += 1
+    assert checked > 100
