@@ -1,0 +1,395 @@
+"""Benchmark: walk-on-stars walk-steps/s on one or more GPUs.
+
+Workload: 2D Poisson on a level-5 Koch snowflake (3072 segments, half
+Dirichlet, half Neumann by arc length) with a 1024-segment random-walk hole
+(all Neumann); exact u = sin 2x cos 3y, f = 13 u; the interior cell centres of
+a 512 x 512 raster (139,674 points), 256 walks per point, eps = r_min = 1e-4.
+A step is one full solve of that workload (every point, every walk).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are replicas: every rank solves
+the whole workload with its own seed (independent walks), no collective is on
+the data path; the timing is the max over ranks.  --impl reference times the
+FP64 brute-force CPU oracle (the only reference this project has) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walk_steps_per_s"
+UNIT = "walk-steps/s"
+WORKLOAD = "koch5_hole_poisson_2d_grid512_w256"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed solves
+
+
+def _config_block(sc, extra=None):
+    cfg = {"workload": WORKLOAD, "n_points": int(len(sc["points"])), "walks_per_point": sc["walks"],
+           "prims": int(len(sc["prims"])), "neumann_prims": int(sc["flags"].sum()), "epsilon": sc["epsilon"],
+           "r_min": sc["r_min"], "max_steps": sc["max_steps"], "precision": "fp32 walks, fp64 accumulators",
+           "l2": "flushed between timed steps (512 MiB write)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# algorithmic cost of one node visit / primitive test, per query (bytes read
+# from the memory hierarchy; FP32 operations with an FMA counted as 2)
+BYTES = {2: {"node": {"q1": 64, "q2": 96, "q3": 64, "q4": 64, "vis": 64},
+             "prim": {"q1": 24, "q2": 32, "q3": 16, "q4": 16, "vis": 16}},
+         3: {"node": {"q1": 64, "q2": 96, "q3": 64, "q4": 64, "vis": 64},
+             "prim": {"q1": 64, "q2": 48, "q3": 48, "q4": 48, "vis": 48}}}
+FLOPS = {2: {"node": {"q1": 24, "q2": 70, "q3": 34, "q4": 44, "vis": 34},
+             "prim": {"q1": 16, "q2": 12, "q3": 16, "q4": 22, "vis": 16}},
+         3: {"node": {"q1": 36, "q2": 90, "q3": 50, "q4": 60, "vis": 50},
+             "prim": {"q1": 45, "q2": 30, "q3": 34, "q4": 50, "vis": 34}}}
+STEP_FLOPS = {2: 60, 3: 80}  # per-step bookkeeping: radius, direction, Green's function, source
+
+
+def work_per_step(counts, steps, dim):
+    b = f = 0.0
+    for q in ("q1", "q2", "q3", "q4", "vis"):
+        b += counts[f"{q}_nodes"] * BYTES[dim]["node"][q] + counts[f"{q}_prims"] * BYTES[dim]["prim"][q]
+        f += counts[f"{q}_nodes"] * FLOPS[dim]["node"][q] + counts[f"{q}_prims"] * FLOPS[dim]["prim"][q]
+    return b / steps, f / steps + STEP_FLOPS[dim]
+
+
+def measure_l2_read_gbs(torch, stream):
+    """Streaming-read bandwidth of a 64 MiB buffer resident in L2."""
+    x = torch.ones(16 << 20, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            x.sum()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(50):
+            x.sum()
+        e.record(stream)
+    e.synchronize()
+    return 50 * x.numel() * 4 / (s.elapsed_time(e) * 1e-3) / 1e9
+
+
+def cpu_baseline(sc, budget_s=15.0, seed=1):
+    """The FP64 oracle as it stands on all host cores, on a bounded sample."""
+    import oracle
+    O = oracle.Scene(sc)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(sc["points"]))
+    cores = os.cpu_count() or 1
+    done_pts = steps = 0
+    t0 = time.perf_counter()
+    k = 0
+    chunk = max(1, cores // 4)
+    while time.perf_counter() - t0 < budget_s and k < len(order):
+        pts = sc["points"][order[k:k + chunk]]
+        r = oracle.solve(O, pts, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed)
+        steps += int(r["steps"].sum())
+        done_pts += len(pts)
+        k += chunk
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done_pts} random points of the workload x {sc['walks']} walks ({steps} steps, {dt:.1f} s)",
+            "points_per_s": done_pts / dt}
+
+
+def run_reference(args):
+    rank, world, local = _dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    from paper_2302_11815_gb300 import scenes
+    sc = scenes.config2()
+    for _ in range(args.warmup):
+        cpu_baseline(sc, budget_s=2.0, seed=99)
+    vals = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        vals.append(cpu_baseline(sc, budget_s=args.ref_seconds, seed=i + 1))
+    elapsed = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config_block(sc, {"sample": "bounded random subsample per step"}),
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v,
+                             "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = _dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2302_11815_gb300 import scenes, wost
+
+    wost.load()  # fails loudly when the CUDA library is missing
+    sc = scenes.config2()
+    pts_host = np.ascontiguousarray(sc["points"], np.float32)
+    n = len(pts_host)
+    walks = sc["walks"]
+    S = wost.Scene(sc, device=local)
+    info = S.info()
+    stream = torch.cuda.Stream()
+    dev_pts = torch.from_numpy(pts_host).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    seed0 = 1000 * (rank + 1)
+
+    def solve_dev(seed):
+        h = wost.wost_solve(S.handle, dev_pts, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed,
+                            kernel=args.kernel, block_size=args.block, stream=stream)
+        return h
+
+    # work counts per step from the counting kernel on a subsample (untimed)
+    sub = torch.from_numpy(pts_host[:: args.count_stride].copy()).cuda()
+    r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting")
+    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2)
+
+    # warm-up
+    for i in range(args.warmup):
+        h = solve_dev(seed0 + 100 + i)
+        wost.wost_wait(h)
+        wost.wost_solve_destroy(h)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    total_steps = 0
+    dev_ms = 0.0
+    kern_s = 0.0
+    capped = 0
+    rms = []
+    u_exact = scenes.exact_u("sin2x_cos3y", (), pts_host)
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))  # evict the scene and accumulators from L2
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h = solve_dev(seed0 + i)
+        ev1.record(stream)
+        ev1.synchronize()
+        dev_ms += ev0.elapsed_time(ev1)
+        mean, se, wd, pr = wost.wost_poll(h, n)
+        wost.wost_solve_destroy(h)
+        total_steps += pr["total_steps"]
+        kern_s += pr["elapsed_seconds"]
+        capped += pr["capped_walks"]
+        rms.append(float(np.sqrt(np.mean((mean - u_exact) ** 2) / np.mean(u_exact ** 2))))
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+
+    t_max = _max_over_ranks(dev_ms * 1e-3, world, "cuda")
+    steps_all = _sum_over_ranks(float(total_steps), world, "cuda")
+    pts_all = _sum_over_ranks(float(n * args.steps), world, "cuda")
+    value = steps_all / t_max
+
+    # end to end through the C ABI with host buffers: host points in, host
+    # estimates out, copies inside the timed region
+    e2e_steps = 0
+    _barrier(world)
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        h = wost.wost_solve(S.handle, pts_host, walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
+                            seed=seed0 + 500 + i, kernel=args.kernel, block_size=args.block)
+        wost.wost_wait(h)
+        mean, se, wd, pr = wost.wost_poll(h, n)
+        wost.wost_solve_destroy(h)
+        e2e_steps += pr["total_steps"]
+    e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
+
+    peaks, peak_src = _measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
+    fp32_peak = 2 * 128 * sms * mhz * 1e6  # FMA = 2 flops, 128 FP32 lanes per SM
+    l2_gbs = measure_l2_read_gbs(torch, stream)
+    kern_avg = kern_s / args.steps
+    steps_per_launch = total_steps / args.steps
+    achieved_b = bytes_step * steps_per_launch / kern_avg / 1e9
+    achieved_f = flops_step * steps_per_launch / kern_avg / 1e12
+    t_mem = bytes_step / (l2_gbs * 1e9)
+    t_alu = flops_step / fp32_peak
+    if t_mem >= t_alu:
+        roof = {"bound": "l2", "achieved": achieved_b, "peak": l2_gbs, "unit": "GB/s", "frac": achieved_b / l2_gbs,
+                "traffic": None}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_f, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved_f / (fp32_peak / 1e12), "traffic": None}
+    roof.update({
+        "kernel": f"k_walk_{args.kernel}<2>", "unit_of_work": "walk step",
+        "bytes_per_step": bytes_step, "flops_per_step": flops_step,
+        "l2_frac": achieved_b / l2_gbs, "l2_peak_gbs": l2_gbs, "l2_peak_src": "measured in this run (64 MiB resident read)",
+        "fp32_frac": achieved_f / (fp32_peak / 1e12), "fp32_peak_tflops": fp32_peak / 1e12,
+        "fp32_peak_src": f"2 x 128 x {sms} SMs x {mhz:.0f} MHz (median SM clock of the run)",
+        "hbm_frac": achieved_b / peaks["hbm_gbs"], "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_src": peak_src,
+        "kernel_ms_avg": 1e3 * kern_avg, "counts_per_step": {k: v / r["total_steps"] for k, v in r["counts"].items()},
+    })
+    if rank == 0:
+        base = cpu_baseline(sc, budget_s=args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config_block(sc, {"kernel": args.kernel, "block": args.block or 128,
+                                         "parallelism": f"replicas x{world}"}),
+            "points_per_s": pts_all / t_max,
+            "rel_rms_error": float(np.mean(rms)), "capped_walks": int(capped),
+            "mean_steps_per_walk": total_steps / (n * walks * args.steps),
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(pts_host.nbytes),
+                    "d2h_bytes_per_step": int(n * 8 * 4 + 4 * 8)},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "roofline": roof,
+            "cpu_baseline": base,
+            "scene": {k: info[k] for k in ("n_dirichlet", "n_neumann", "n_silhouette", "nodes_dirichlet",
+                                           "nodes_neumann", "nodes_silhouette", "depth_dirichlet",
+                                           "depth_neumann", "depth_silhouette", "device_bytes", "build_seconds")},
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="persistent", choices=["plain", "persistent"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--count-stride", type=int, default=16)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * wost.h -- C ABI of the GB300 walk-on-stars library (libwost.so).
+ *
+ * Method: Sawhney, Miller, Gkioulekas, Crane, "Walk on Stars: A Grid-Free
+ * Monte Carlo Method for PDEs with Neumann Boundary Conditions", ACM TOG
+ * 42(4), 2023 (arXiv 2302.11815).
+ *
+ * Problem solved (Sec. 3.2, Eq. PoissonEquation, with the sign convention of
+ * the positive Green's functions of App. A.1):
+ *
+ *     -Lap u = f   in Omega,
+ *          u = g   on the Dirichlet boundary,
+ *      du/dn = h   on the Neumann boundary (n = outward unit normal),
+ *
+ * estimated at caller-chosen points by independent random walks (Alg. 1),
+ * each step using a star-shaped region whose radius is the smaller of the
+ * distance to the Dirichlet boundary (query Q.1) and the distance to the
+ * visibility silhouette of the Neumann boundary (Q.2, Sec. 5.1), a ray cast
+ * against the Neumann boundary (Q.3) and a hierarchical Neumann sample (Q.4,
+ * Sec. 5.2).  Walks run on the GPU in single precision; per-point sums are
+ * accumulated in double precision.
+ *
+ * Conventions for every call:
+ *   - Every call returns a wost_status; nothing throws or aborts across the
+ *     ABI.  On failure, wost_last_error() gives a message (thread-local).
+ *   - The library copies every input array during the call; the caller keeps
+ *     ownership and may free its arrays as soon as the call returns.
+ *   - Output arrays are caller-owned and sized as stated.
+ *   - Handles are opaque; the caller destroys what it creates.
+ *   - Geometry: dim = 2 (line segments, 2 vertex indices each) or 3
+ *     (triangles, 3 indices).  A 2D segment a->b has outward normal
+ *     (t.y, -t.x), t = (b-a)/|b-a|; a 3D triangle a,b,c has outward normal
+ *     (b-a)x(c-a)/|..|.  Degenerate primitives (zero length or area) are
+ *     dropped and counted.  The boundary need not be watertight (Sec. 5).
+ */
+#ifndef WOST_H
+#define WOST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WOST_ABI_VERSION 1
+
+typedef enum {
+    WOST_OK = 0,
+    WOST_ERR_INVALID_ARG = 1, /* bad pointer, size, index, value or mode     */
+    WOST_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed          */
+    WOST_ERR_BUDGET = 3,      /* request exceeds the engine's memory budget  */
+    WOST_ERR_CUDA = 4,        /* a CUDA runtime call failed                  */
+    WOST_ERR_TIMEOUT = 5,     /* wost_wait gave up before completion         */
+    WOST_ERR_CANCELLED = 6,   /* the solve was cancelled                     */
+    WOST_ERR_INTERNAL = 7     /* a device-side guard fired (see progress)    */
+} wost_status;
+
+/* ---------------------------------------------------------------------- */
+/* Boundary data and source (Sec. 3.2: g on the Dirichlet part, h on the   */
+/* Neumann part, f inside).                                                */
+/* ---------------------------------------------------------------------- */
+typedef enum {
+    WOST_DATA_NONE = 0,       /* absent: zero (f only)                         */
+    WOST_DATA_PER_VERTEX = 1, /* values[n_vertices], linear on each primitive */
+    WOST_DATA_PER_CORNER = 2, /* values[n_prims*dim], one per primitive corner */
+    WOST_DATA_ANALYTIC = 3,   /* built-in exact solution `fn`: g = u,
+                                 h = grad u . n, f = -Lap u                    */
+    WOST_DATA_GRID = 4        /* f only: node-centred grid, dims[0] fastest,
+                                 (bi/tri)linear, clamped at the edges          */
+} wost_data_kind;
+
+typedef enum {
+    WOST_FN_ZERO = 0,
+    WOST_FN_EXP_COS = 1,     /* u = e^x cos y                                  */
+    WOST_FN_SIN2X_COS3Y = 2, /* u = sin 2x cos 3y (2D), -Lap u = 13 u          */
+    WOST_FN_QUAD3 = 3,       /* u = x^2 - y^2 + z/2                            */
+    WOST_FN_BUMP = 4,        /* u = (1 - |x|^2)/(2 dim), -Lap u = 1            */
+    WOST_FN_LINEAR = 5,      /* u = p0 + p1 x + p2 y + p3 z                    */
+    WOST_FN_LOG_RADIAL = 6   /* 2D p0 + p1 log|x-c|, 3D p0 + p1/|x-c|,
+                                c = (p2, p3, p4)                               */
+} wost_fn;
+
+typedef struct {
+    int32_t kind;          /* wost_data_kind                                 */
+    const float *values;   /* host array for PER_VERTEX / PER_CORNER / GRID  */
+    int32_t fn;            /* ANALYTIC: wost_fn                              */
+    float params[8];       /* ANALYTIC parameters                            */
+    float origin[3];       /* GRID: position of node (0,0,0)                 */
+    float spacing[3];      /* GRID: node spacing (> 0)                       */
+    int32_t dims[3];       /* GRID: nodes per axis (>= 1; dims[2] ignored in 2D) */
+} wost_field;
+
+/* ---------------------------------------------------------------------- */
+/* Scenes: the boundary, its hierarchies (a BVH over the Dirichlet part, a */
+/* BVH and a spatialized normal-cone hierarchy over the Neumann part,      */
+/* Sec. 5 and 5.1.1) and boundary data, resident on one device.            */
+/* ---------------------------------------------------------------------- */
+typedef struct wost_scene wost_scene;
+
+typedef struct {
+    int32_t dim;               /* 2 or 3                                       */
+    int64_t n_vertices;
+    const float *vertices;     /* host [n_vertices * dim]                      */
+    int64_t n_prims;
+    const int32_t *prims;      /* host [n_prims * dim], indices < n_vertices   */
+    const uint8_t *flags;      /* host [n_prims]: 0 Dirichlet, 1 Neumann       */
+    wost_field g, h, f;
+    int32_t device;            /* CUDA device ordinal                          */
+    int32_t leaf_size;         /* primitives per leaf, 0 = default (4)         */
+} wost_scene_desc;
+
+typedef struct {
+    int32_t dim;
+    int64_t n_dirichlet, n_neumann, n_silhouette, n_dropped;
+    int64_t nodes_dirichlet, nodes_neumann, nodes_silhouette;
+    int32_t depth_dirichlet, depth_neumann, depth_silhouette;
+    int64_t device_bytes;      /* bytes of resident scene data               */
+    double build_seconds;
+    float bbox_lo[3], bbox_hi[3];
+} wost_scene_info;
+
+/* Builds the hierarchies on the host, uploads them, returns a handle.
+ * Errors: INVALID_ARG for dim not 2/3, null arrays, an index out of range, a
+ * flag > 1, non-finite coordinates, a field whose values are missing, no
+ * Dirichlet primitive (pure Neumann problems need the regularisation of
+ * Sec. 6.4, which this library does not provide); OUT_OF_MEMORY; CUDA. */
+wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out);
+wost_status wost_scene_destroy(wost_scene *scene);
+wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out);
+
+/* ---------------------------------------------------------------------- */
+/* Solves: n points x walks_per_point walks of Alg. 1.                     */
+/* ---------------------------------------------------------------------- */
+typedef struct wost_solve_handle wost_solve_handle;
+
+typedef enum {
+    WOST_MEM_HOST = 0,   /* points / normals / on_neumann are host pointers   */
+    WOST_MEM_DEVICE = 1  /* ... are device pointers on the scene's device      */
+} wost_memory;
+
+typedef enum {
+    WOST_KERNEL_PLAIN = 0,      /* one thread per walk, one launch             */
+    WOST_KERNEL_PERSISTENT = 1, /* persistent lanes that regenerate finished
+                                   walks from a work counter                   */
+    WOST_KERNEL_COUNTING = 2    /* the plain kernel plus per-query work
+                                   counters (see wost_solve_work_counts)       */
+} wost_kernel;
+
+typedef struct {
+    int64_t n_points;
+    const float *points;       /* [n_points * dim]                             */
+    const float *normals;      /* optional [n_points * dim]: outward normal of
+                                  points on the Neumann boundary (Alg. 1 n_x)  */
+    const uint8_t *on_neumann; /* optional [n_points]: 1 if on the Neumann part */
+    int32_t memory;            /* wost_memory of the three arrays above        */
+    int32_t walks_per_point;   /* >= 1                                         */
+    float epsilon;             /* epsilon-shell width (> 0)                    */
+    float r_min;               /* minimum star radius, 0 < r_min (0 = epsilon) */
+    int32_t max_steps;         /* step cap per walk (>= 1)                     */
+    uint64_t seed;             /* Philox key                                   */
+    uint32_t first_walk;       /* walk index of the first walk of every point  */
+    int32_t kernel;            /* wost_kernel                                  */
+    int32_t block_size;        /* threads per block, 0 = tuned default         */
+    void *stream;              /* cudaStream_t to run on, NULL = library stream */
+} wost_solve_desc;
+
+typedef struct {
+    int32_t done;              /* 1 once every walk has finished               */
+    uint64_t walks_done;       /* walks accumulated so far                     */
+    uint64_t total_steps;      /* walk steps (each Q.1 evaluation is a step)   */
+    uint64_t capped_walks;     /* walks stopped by max_steps                   */
+    uint32_t guard_flags;      /* device guards: 1 = traversal stack overflow  */
+    double elapsed_seconds;    /* from launch to completion (or to now)        */
+} wost_progress;
+
+/* Starts a solve asynchronously on the stream and returns its handle.
+ * The caller's arrays are copied before return.  Errors: INVALID_ARG
+ * (n_points < 1, walks < 1, epsilon <= 0, r_min > epsilon, max_steps < 1,
+ * a null points array), OUT_OF_MEMORY, CUDA. */
+wost_status wost_solve(wost_scene *scene, const wost_solve_desc *desc, wost_solve_handle **out);
+
+/* Snapshot of the running estimates.  mean and stderr_ (host, n_points each)
+ * may be NULL.  stderr_ is sqrt(sample variance / walks); walks_done
+ * (host, n_points, may be NULL) is the per-point walk count. */
+wost_status wost_poll(wost_solve_handle *solve, double *mean, double *stderr_, uint64_t *walks_done,
+                      wost_progress *progress);
+
+/* Blocks until the solve finishes or timeout_s elapses (< 0: no limit).
+ * Returns TIMEOUT on expiry, INTERNAL if a device guard fired. */
+wost_status wost_wait(wost_solve_handle *solve, double timeout_s);
+
+/* Stops a solve at the next walk boundary (walks already accumulated stay). */
+wost_status wost_cancel(wost_solve_handle *solve);
+wost_status wost_solve_destroy(wost_solve_handle *solve);
+
+/* Device pointers to the per-point FP64 accumulators of a solve (valid until
+ * destroy): sum and sum of squares of the walk estimates, walk and step
+ * counts. */
+wost_status wost_solve_device_accumulators(wost_solve_handle *solve, const double **sum,
+                                           const double **sumsq, const uint64_t **walks,
+                                           const uint64_t **steps);
+
+/* Work done by a WOST_KERNEL_COUNTING solve (after wost_wait): counts[0..4]
+ * are node visits of Q.1, Q.2, Q.3, Q.4 and of the visibility ray of the
+ * Neumann sample; counts[5..9] the primitive tests of the same queries.
+ * INVALID_ARG for a solve started with another kernel. */
+wost_status wost_solve_work_counts(wost_solve_handle *solve, uint64_t counts[10]);
+
+/* ---------------------------------------------------------------------- */
+/* Batched geometric queries (Sec. 5, Q.1-Q.4), for checking and reuse.    */
+/* All arrays are DEVICE pointers; points/vectors are [n * dim] floats.    */
+/* ---------------------------------------------------------------------- */
+
+/* Q.1: distance to the closest Dirichlet point, that point, and the
+ * primitive (input index), or +inf and -1 without Dirichlet primitives. */
+wost_status wost_query_closest_dirichlet(wost_scene *scene, int64_t n, const float *points,
+                                         float *dist, float *closest, int32_t *prim, void *stream);
+
+/* Q.2 (Algs. 2-4): distance to the closest visibility-silhouette point of
+ * the Neumann boundary within rmax[i]; rmax[i] if there is none. */
+wost_status wost_query_silhouette(wost_scene *scene, int64_t n, const float *points,
+                                  const float *rmax, float *dist, void *stream);
+
+/* Q.3: first hit of origin + t dir, 0 < t <= tmax[i], with the Neumann
+ * boundary; skip[i] (input index or -1, may be NULL) is ignored.  hit is 0/1,
+ * t the distance along dir (unnormalised dir scales t), prim the input
+ * index or -1. */
+wost_status wost_query_intersect_neumann(wost_scene *scene, int64_t n, const float *origins,
+                                         const float *dirs, const float *tmax, const int32_t *skip,
+                                         int32_t *hit, float *t, int32_t *prim, void *stream);
+
+/* Q.4 (Algs. 5-6): for ball i (center points[i], radius r[i]) one Neumann
+ * sample z (n * dim), its density pdf (0 if none) and primitive (input index
+ * or -1), drawn from the Philox stream key = seed, counter = (i, ctr1,
+ * ctr2, 1, 2, ...). */
+wost_status wost_query_neumann_sample(wost_scene *scene, int64_t n, const float *points,
+                                      const float *r, uint64_t seed, uint32_t ctr1, uint32_t ctr2,
+                                      float *z, float *pdf, int32_t *prim, void *stream);
+
+/* Thread-local description of the last failure on this thread. */
+const char *wost_last_error(void);
+int32_t wost_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WOST_H */

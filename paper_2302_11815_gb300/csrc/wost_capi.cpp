@@ -1,0 +1,508 @@
+// C ABI of libwost (include/wost.h): scenes, solves, queries, errors.
+//
+// Nothing throws across the ABI: every entry point catches, records a
+// thread-local message and returns a status.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/wost.h"
+#include "scene_build.h"
+#include "wost_kernels.h"
+
+using namespace wost;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+wost_status fail(wost_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+wost_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? WOST_ERR_OUT_OF_MEMORY : WOST_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(expr, what)                              \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// device allocation owned by a scene or solve
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n) {
+        bytes = n;
+        return n ? cudaMalloc(&p, n) : cudaSuccess;
+    }
+};
+
+template <class T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v) {
+    cudaError_t e = b.alloc(v.size() * sizeof(T));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+struct wost_scene {
+    int device = 0;
+    HostScene host;
+    SceneView view{};
+    DevBuf bufs[16];
+    DevBuf n_rec_of_id;
+    unsigned int *guard = nullptr;  // device guard word for query kernels
+    wost_scene_info info{};
+    int stack_depth = 0;
+    std::mutex mu;
+    ~wost_scene() {
+        if (guard) cudaFree(guard);
+    }
+};
+
+struct wost_solve_handle {
+    wost_scene *scene = nullptr;
+    int device = 0;
+    int dim = 2;
+    int64_t n_points = 0;
+    int32_t walks = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t poll_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    DevBuf points, normals, onN;
+    DevBuf sum, sumsq, walks_done, steps, globals;  // globals: capped, next_walk, guard
+    DevBuf counts;                                   // counting kernel only
+    int kernel = 0;
+    int *cancel_host = nullptr;                      // mapped pinned
+    int *cancel_dev = nullptr;
+    std::chrono::steady_clock::time_point t_launch;
+    double elapsed_done = -1;
+    bool done = false;
+    std::mutex mu;
+    ~wost_solve_handle() {
+        if (stream) cudaStreamSynchronize(stream);
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_done) cudaEventDestroy(ev_done);
+        if (poll_stream) cudaStreamDestroy(poll_stream);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        if (cancel_host) cudaFreeHost(cancel_host);
+    }
+};
+
+extern "C" {
+
+const char *wost_last_error(void) { return g_last_error.c_str(); }
+int32_t wost_abi_version(void) { return WOST_ABI_VERSION; }
+
+wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
+    try {
+        if (!desc || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+        *out = nullptr;
+        if (desc->device < 0) return fail(WOST_ERR_INVALID_ARG, "device ordinal out of range");
+        std::unique_ptr<wost_scene> s(new wost_scene);
+        s->device = desc->device;
+        // host-side validation and build first: bad input is rejected without
+        // touching the device
+        std::string err = build_scene(*desc, s->host);
+        if (!err.empty()) return fail(WOST_ERR_INVALID_ARG, err);
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+        if (desc->device >= ndev) return fail(WOST_ERR_INVALID_ARG, "device ordinal out of range");
+        CK(cudaSetDevice(s->device), "cudaSetDevice");
+        HostScene &H = s->host;
+        HostTree *trees[3] = {&H.D, &H.N, &H.S};
+        TreeView *views[3] = {&s->view.D, &s->view.N, &s->view.S};
+        int64_t bytes = 0;
+        for (int t = 0; t < 3; ++t) {
+            HostTree &T = *trees[t];
+            DevBuf *b = &s->bufs[5 * t];
+            CK(upload(b[0], T.nodes), "upload nodes");
+            CK(upload(b[1], T.cones), "upload cones");
+            CK(upload(b[2], T.prims), "upload prims");
+            CK(upload(b[3], T.data), "upload data");
+            CK(upload(b[4], T.ids), "upload ids");
+            for (int k = 0; k < 5; ++k) bytes += (int64_t)b[k].bytes;
+            TreeView &V = *views[t];
+            V.nodes = (const float4 *)b[0].p;
+            V.cones = (const float4 *)b[1].p;
+            V.prims = (const float4 *)b[2].p;
+            V.data = (const float4 *)b[3].p;
+            V.ids = (const int32_t *)b[4].p;
+            V.root = T.root;
+            for (int a = 0; a < 3; ++a) {
+                V.root_lo[a] = T.root_lo[a];
+                V.root_hi[a] = T.root_hi[a];
+            }
+            V.root_cone = T.root_cone;
+            V.n_prims = T.n_prims;
+            V.n_nodes = T.n_nodes;
+            V.depth = T.depth;
+        }
+        CK(upload(s->bufs[15], H.grid), "upload grid");
+        bytes += (int64_t)s->bufs[15].bytes;
+        std::vector<int32_t> rec_of_id((size_t)desc->n_prims, -1);
+        for (size_t k = 0; k < H.N.ids.size(); ++k) rec_of_id[H.N.ids[k]] = (int32_t)k;
+        CK(upload(s->n_rec_of_id, rec_of_id), "upload map");
+        CK(cudaMalloc(&s->guard, sizeof(unsigned int)), "cudaMalloc guard");
+        CK(cudaMemset(s->guard, 0, sizeof(unsigned int)), "cudaMemset guard");
+        s->view.dim = H.dim;
+        s->view.g = H.g;
+        s->view.h = H.h;
+        s->view.f = H.f;
+        s->view.f.grid = (const float *)s->bufs[15].p;
+        s->stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
+        wost_scene_info &I = s->info;
+        I.dim = H.dim;
+        I.n_dirichlet = H.n_dirichlet;
+        I.n_neumann = H.n_neumann;
+        I.n_silhouette = H.n_silhouette;
+        I.n_dropped = H.n_dropped;
+        I.nodes_dirichlet = H.D.n_nodes;
+        I.nodes_neumann = H.N.n_nodes;
+        I.nodes_silhouette = H.S.n_nodes;
+        I.depth_dirichlet = H.D.depth;
+        I.depth_neumann = H.N.depth;
+        I.depth_silhouette = H.S.depth;
+        I.device_bytes = bytes;
+        I.build_seconds = H.build_seconds;
+        for (int a = 0; a < 3; ++a) {
+            I.bbox_lo[a] = H.lo[a];
+            I.bbox_hi[a] = H.hi[a];
+        }
+        *out = s.release();
+        return WOST_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WOST_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
+wost_status wost_scene_destroy(wost_scene *scene) {
+    if (!scene) return fail(WOST_ERR_INVALID_ARG, "null scene");
+    cudaSetDevice(scene->device);
+    delete scene;
+    return WOST_OK;
+}
+
+wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out) {
+    if (!scene || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+    *out = scene->info;
+    return WOST_OK;
+}
+
+wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_handle **out) {
+    try {
+        if (!scene || !d || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+        *out = nullptr;
+        if (d->n_points < 1 || !d->points) return fail(WOST_ERR_INVALID_ARG, "points missing");
+        if (d->n_points > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "more than 2^32-1 points");
+        if (d->walks_per_point < 1) return fail(WOST_ERR_INVALID_ARG, "walks_per_point must be >= 1");
+        if (!(d->epsilon > 0) || !std::isfinite(d->epsilon)) return fail(WOST_ERR_INVALID_ARG, "epsilon must be > 0");
+        float rmin = d->r_min == 0 ? d->epsilon : d->r_min;
+        if (!(rmin > 0) || rmin > d->epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
+        if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
+        if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
+            return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
+        if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING)
+            return fail(WOST_ERR_INVALID_ARG, "unknown kernel");
+        int block = d->block_size ? d->block_size : 128;
+        if (block < 32 || block > 256 || block % 32) return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
+        CK(cudaSetDevice(scene->device), "cudaSetDevice");
+        std::unique_ptr<wost_solve_handle> h(new wost_solve_handle);
+        h->scene = scene;
+        h->device = scene->device;
+        h->dim = scene->view.dim;
+        h->n_points = d->n_points;
+        h->walks = d->walks_per_point;
+        h->kernel = d->kernel;
+        const int dim = h->dim;
+        if (d->stream) {
+            h->stream = (cudaStream_t)d->stream;
+        } else {
+            CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            h->own_stream = true;
+        }
+        CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        CK(cudaEventCreate(&h->ev_start), "cudaEventCreate");
+        CK(cudaEventCreate(&h->ev_done), "cudaEventCreate");
+        const size_t n = (size_t)d->n_points;
+        CK(h->points.alloc(n * dim * sizeof(float)), "cudaMalloc points");
+        cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, h->stream), "copy points");
+        if (d->normals && d->on_neumann) {
+            CK(h->normals.alloc(n * dim * sizeof(float)), "cudaMalloc normals");
+            CK(h->onN.alloc(n), "cudaMalloc on_neumann");
+            CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, h->stream), "copy normals");
+            CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, h->stream), "copy on_neumann");
+        }
+        CK(h->sum.alloc(n * 8), "cudaMalloc accumulators");
+        CK(h->sumsq.alloc(n * 8), "cudaMalloc accumulators");
+        CK(h->walks_done.alloc(n * 8), "cudaMalloc accumulators");
+        CK(h->steps.alloc(n * 8), "cudaMalloc accumulators");
+        CK(h->globals.alloc(4 * 8), "cudaMalloc accumulators");
+        CK(cudaMemsetAsync(h->sum.p, 0, n * 8, h->stream), "memset");
+        CK(cudaMemsetAsync(h->sumsq.p, 0, n * 8, h->stream), "memset");
+        CK(cudaMemsetAsync(h->walks_done.p, 0, n * 8, h->stream), "memset");
+        CK(cudaMemsetAsync(h->steps.p, 0, n * 8, h->stream), "memset");
+        CK(cudaMemsetAsync(h->globals.p, 0, 4 * 8, h->stream), "memset");
+        CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+        *h->cancel_host = 0;
+        CK(cudaHostGetDevicePointer((void **)&h->cancel_dev, h->cancel_host, 0), "cudaHostGetDevicePointer");
+        // the caller's arrays may be released on return: wait for the copies
+        cudaEvent_t copied;
+        CK(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming), "cudaEventCreate");
+        cudaEventRecord(copied, h->stream);
+        cudaError_t ce = cudaEventSynchronize(copied);
+        cudaEventDestroy(copied);
+        if (ce != cudaSuccess) return cuda_fail(ce, "input copy");
+
+        SolveParams sp{};
+        sp.points = (const float *)h->points.p;
+        sp.normals = (const float *)h->normals.p;
+        sp.on_neumann = (const uint8_t *)h->onN.p;
+        sp.n_points = d->n_points;
+        sp.walks_per_point = d->walks_per_point;
+        sp.first_walk = d->first_walk;
+        sp.epsilon = d->epsilon;
+        sp.r_min = rmin;
+        sp.max_steps = d->max_steps;
+        sp.key0 = (uint32_t)d->seed;
+        sp.key1 = (uint32_t)(d->seed >> 32);
+        sp.offset = 1e-6f;
+        sp.vis_tmax = 1.f - 1e-4f;
+        sp.stack_depth = scene->stack_depth;
+        Accumulators acc{};
+        acc.sum = (double *)h->sum.p;
+        acc.sumsq = (double *)h->sumsq.p;
+        acc.walks = (unsigned long long *)h->walks_done.p;
+        acc.steps = (unsigned long long *)h->steps.p;
+        unsigned long long *g = (unsigned long long *)h->globals.p;
+        acc.capped = g;
+        acc.next_walk = g + 1;
+        acc.guard = (unsigned int *)(g + 2);
+        acc.cancel = h->cancel_dev;
+        h->t_launch = std::chrono::steady_clock::now();
+        CK(cudaEventRecord(h->ev_start, h->stream), "cudaEventRecord");
+        cudaError_t le;
+        if (d->kernel == WOST_KERNEL_PLAIN) {
+            le = launch_walk_plain(scene->view, sp, acc, block, h->stream);
+        } else if (d->kernel == WOST_KERNEL_COUNTING) {
+            le = h->counts.alloc(10 * 8);
+            if (le == cudaSuccess) le = cudaMemsetAsync(h->counts.p, 0, 10 * 8, h->stream);
+            if (le == cudaSuccess)
+                le = launch_walk_count(scene->view, sp, acc, (unsigned long long *)h->counts.p, block, h->stream);
+        } else {
+            int blocks = 0;
+            le = persistent_grid(dim, block, sp.stack_depth, &blocks);
+            if (le == cudaSuccess) le = launch_walk_persistent(scene->view, sp, acc, block, blocks, h->stream);
+        }
+        if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
+        CK(cudaEventRecord(h->ev_done, h->stream), "cudaEventRecord");
+        *out = h.release();
+        return WOST_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WOST_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
+static wost_status check_done(wost_solve_handle *h) {
+    if (h->done) return WOST_OK;
+    cudaError_t q = cudaEventQuery(h->ev_done);
+    if (q == cudaSuccess) {
+        h->done = true;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev_start, h->ev_done);
+        h->elapsed_done = ms * 1e-3;
+        return WOST_OK;
+    }
+    if (q != cudaErrorNotReady) return cuda_fail(q, "solve");
+    return WOST_OK;
+}
+
+wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *walks_done, wost_progress *pr) {
+    try {
+        if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+        std::lock_guard<std::mutex> lk(h->mu);
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        wost_status st = check_done(h);
+        if (st != WOST_OK) return st;
+        bool was_done = h->done;
+        const size_t n = (size_t)h->n_points;
+        std::vector<double> s(n), q(n);
+        std::vector<unsigned long long> w(n), stp(n), glob(4);
+        CK(cudaMemcpyAsync(s.data(), h->sum.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        CK(cudaMemcpyAsync(q.data(), h->sumsq.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        CK(cudaMemcpyAsync(w.data(), h->walks_done.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        if (pr) CK(cudaMemcpyAsync(stp.data(), h->steps.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        CK(cudaMemcpyAsync(glob.data(), h->globals.p, 4 * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        CK(cudaStreamSynchronize(h->poll_stream), "poll sync");
+        uint64_t tw = 0, ts = 0;
+        for (size_t i = 0; i < n; ++i) {
+            double c = (double)w[i];
+            double m = c > 0 ? s[i] / c : 0.0;
+            if (mean) mean[i] = m;
+            if (se) {
+                double var = c > 1 ? std::max(0.0, (q[i] - c * m * m) / (c - 1.0)) : 0.0;
+                se[i] = c > 0 ? std::sqrt(var / c) : 0.0;
+            }
+            if (walks_done) walks_done[i] = w[i];
+            tw += w[i];
+            if (pr) ts += stp[i];
+        }
+        if (pr) {
+            pr->done = was_done ? 1 : 0;
+            pr->walks_done = tw;
+            pr->total_steps = ts;
+            pr->capped_walks = glob[0];
+            pr->guard_flags = (uint32_t)glob[2];
+            pr->elapsed_seconds = was_done ? h->elapsed_done
+                                           : std::chrono::duration<double>(std::chrono::steady_clock::now() - h->t_launch).count();
+        }
+        if ((uint32_t)glob[2]) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+        return WOST_OK;
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
+wost_status wost_wait(wost_solve_handle *h, double timeout_s) {
+    if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(h->mu);
+            wost_status st = check_done(h);
+            if (st != WOST_OK) return st;
+            if (h->done) break;
+        }
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_s >= 0 && el >= timeout_s) return fail(WOST_ERR_TIMEOUT, "solve not finished");
+        std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 500));
+    }
+    unsigned long long glob[4];
+    CK(cudaMemcpy(glob, h->globals.p, sizeof glob, cudaMemcpyDeviceToHost), "copy guard");
+    if ((uint32_t)glob[2]) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+    if (*(volatile int *)h->cancel_host) return fail(WOST_ERR_CANCELLED, "solve was cancelled");
+    return WOST_OK;
+}
+
+wost_status wost_cancel(wost_solve_handle *h) {
+    if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+    *(volatile int *)h->cancel_host = 1;
+    return WOST_OK;
+}
+
+wost_status wost_solve_destroy(wost_solve_handle *h) {
+    if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+    cudaSetDevice(h->device);
+    delete h;
+    return WOST_OK;
+}
+
+wost_status wost_solve_device_accumulators(wost_solve_handle *h, const double **sum, const double **sumsq,
+                                           const uint64_t **walks, const uint64_t **steps) {
+    if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+    if (sum) *sum = (const double *)h->sum.p;
+    if (sumsq) *sumsq = (const double *)h->sumsq.p;
+    if (walks) *walks = (const uint64_t *)h->walks_done.p;
+    if (steps) *steps = (const uint64_t *)h->steps.p;
+    return WOST_OK;
+}
+
+wost_status wost_solve_work_counts(wost_solve_handle *h, uint64_t counts[10]) {
+    if (!h || !counts) return fail(WOST_ERR_INVALID_ARG, "null argument");
+    if (h->kernel != WOST_KERNEL_COUNTING) return fail(WOST_ERR_INVALID_ARG, "solve was not started with the counting kernel");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaEventSynchronize(h->ev_done), "solve");
+    CK(cudaMemcpy(counts, h->counts.p, 10 * 8, cudaMemcpyDeviceToHost), "copy counts");
+    return WOST_OK;
+}
+
+// ------------------------------- queries ---------------------------------
+static wost_status query_prologue(wost_scene *s, int64_t n) {
+    if (!s) return fail(WOST_ERR_INVALID_ARG, "null scene");
+    if (n < 0) return fail(WOST_ERR_INVALID_ARG, "negative count");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    return WOST_OK;
+}
+static wost_status query_epilogue(wost_scene *s, cudaError_t e, cudaStream_t st) {
+    if (e != cudaSuccess) return cuda_fail(e, "query launch");
+    unsigned int g = 0;
+    CK(cudaMemcpyAsync(&g, s->guard, sizeof g, cudaMemcpyDeviceToHost, st), "copy guard");
+    CK(cudaStreamSynchronize(st), "query sync");
+    if (g) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+    return WOST_OK;
+}
+
+wost_status wost_query_closest_dirichlet(wost_scene *s, int64_t n, const float *pts, float *dist, float *closest,
+                                         int32_t *prim, void *stream) {
+    wost_status st = query_prologue(s, n);
+    if (st != WOST_OK) return st;
+    if (!n) return WOST_OK;
+    if (!pts || !dist || !closest || !prim) return fail(WOST_ERR_INVALID_ARG, "null array");
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaError_t e = launch_query_closest(s->view, n, pts, dist, closest, prim, s->stack_depth, s->guard,
+                                         (cudaStream_t)stream);
+    return query_epilogue(s, e, (cudaStream_t)stream);
+}
+
+wost_status wost_query_silhouette(wost_scene *s, int64_t n, const float *pts, const float *rmax, float *dist,
+                                  void *stream) {
+    wost_status st = query_prologue(s, n);
+    if (st != WOST_OK) return st;
+    if (!n) return WOST_OK;
+    if (!pts || !rmax || !dist) return fail(WOST_ERR_INVALID_ARG, "null array");
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaError_t e = launch_query_silhouette(s->view, n, pts, rmax, dist, s->stack_depth, s->guard, (cudaStream_t)stream);
+    return query_epilogue(s, e, (cudaStream_t)stream);
+}
+
+wost_status wost_query_intersect_neumann(wost_scene *s, int64_t n, const float *o, const float *v, const float *tmax,
+                                         const int32_t *skip, int32_t *hit, float *t, int32_t *prim, void *stream) {
+    wost_status st = query_prologue(s, n);
+    if (st != WOST_OK) return st;
+    if (!n) return WOST_OK;
+    if (!o || !v || !tmax || !hit || !t || !prim) return fail(WOST_ERR_INVALID_ARG, "null array");
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaError_t e = launch_query_ray(s->view, n, o, v, tmax, skip, (const int32_t *)s->n_rec_of_id.p,
+                                     (int64_t)(s->n_rec_of_id.bytes / sizeof(int32_t)), hit, t, prim, s->stack_depth,
+                                     s->guard, (cudaStream_t)stream);
+    return query_epilogue(s, e, (cudaStream_t)stream);
+}
+
+wost_status wost_query_neumann_sample(wost_scene *s, int64_t n, const float *pts, const float *r, uint64_t seed,
+                                      uint32_t ctr1, uint32_t ctr2, float *z, float *pdf, int32_t *prim,
+                                      void *stream) {
+    wost_status st = query_prologue(s, n);
+    if (st != WOST_OK) return st;
+    if (!n) return WOST_OK;
+    if (!pts || !r || !z || !pdf || !prim) return fail(WOST_ERR_INVALID_ARG, "null array");
+    if (n > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "too many queries");
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaError_t e = launch_query_sample(s->view, n, pts, r, (uint32_t)seed, (uint32_t)(seed >> 32), ctr1, ctr2, z, pdf,
+                                        prim, (cudaStream_t)stream);
+    return query_epilogue(s, e, (cudaStream_t)stream);
+}
+
+}  // extern "C"

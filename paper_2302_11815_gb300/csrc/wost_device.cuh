@@ -1,0 +1,869 @@
+// Device code of the walk-on-stars hot path (single precision, sm_103a).
+//
+// Paper: Sawhney et al., "Walk on Stars", 2023.  One call of walk_step() is
+// one iteration of Alg. 1: Q.1 closest Dirichlet point, epsilon-shell test,
+// Q.2 silhouette distance within d_D, star radius, direction (hemisphere on
+// the Neumann boundary, Sec. 4.4.2), Q.3 first Neumann hit, Q.4 Neumann
+// sample with its visibility test (Sec. 4.5, Algs. 5-6), source sample
+// reusing the direction (Sec. 4.6), and the move.  Readings of the paper
+// used here (also listed in the design notes):
+//   R1 each step adds +N + S (App. A's positive Green's functions, outward h);
+//   R2 d_sil is the minimum over silhouette candidates within d_D (Alg. 3's
+//      Ensure line);
+//   R3 r = min(d_D, max(r_min, d_sil));
+//   R4 on the Neumann boundary Q.2/Q.3/visibility start at x - delta n_x,
+//      delta = offset (1 + |x|_inf); the visibility ray skips z's primitive
+//      and stops at vis_tmax;
+//   R5 at the step cap the walk ends with g at the closest Dirichlet point;
+//   R6 Q.4 child weight 1/d to the child box centre (the 1/(4 pi) of the
+//      free-space Green's function cancels in the child probabilities);
+//   R7 2D source radius R sqrt(U1 U2), 3D R (1/2 + sin(asin(2U-1)/3)).
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11); key = seed, counter
+// = (walk, point, step, slot); slot 0 drives direction and source, slots
+// 1, 2, ... the Neumann sampler.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wost_internal.h"
+
+namespace wost {
+
+// ---------------------------------------------------------------------------
+// vectors (3 components; z stays 0 in 2D)
+// ---------------------------------------------------------------------------
+struct P3 {
+    float x, y, z;
+};
+__device__ __forceinline__ P3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ P3 operator+(P3 a, P3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ P3 operator-(P3 a, P3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ P3 operator*(P3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+template <int D>
+__device__ __forceinline__ float dotp(P3 a, P3 b) {
+    float r = a.x * b.x + a.y * b.y;
+    if constexpr (D == 3) r += a.z * b.z;
+    return r;
+}
+__device__ __forceinline__ P3 crossp(P3 a, P3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+// (0,1): top 23 bits plus one half, times 2^-23 (exact in FP32)
+__device__ __forceinline__ float u01(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+
+struct Stream {  // sequential uniforms from slots 1, 2, ... of one (walk, point, step)
+    uint4 ctr;
+    uint32_t k0, k1;
+    uint4 buf;
+    int used;
+    __device__ __forceinline__ void init(uint32_t key0, uint32_t key1, uint32_t c0, uint32_t c1, uint32_t c2) {
+        ctr = make_uint4(c0, c1, c2, 1u);
+        k0 = key0;
+        k1 = key1;
+        used = 4;
+    }
+    __device__ __forceinline__ float next() {
+        if (used == 4) {
+            buf = philox10(ctr, k0, k1);
+            ctr.w += 1u;
+            used = 0;
+        }
+        uint32_t w = used == 0 ? buf.x : (used == 1 ? buf.y : (used == 2 ? buf.z : buf.w));
+        ++used;
+        return u01(w);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// work counters (compiled in only for the counting kernel): per query, node
+// visits and primitive tests
+// ---------------------------------------------------------------------------
+enum { C_Q1 = 0, C_Q2 = 1, C_Q3 = 2, C_Q4 = 3, C_VIS = 4, C_NQ = 5 };
+template <bool ON>
+struct Cnt {
+    __device__ __forceinline__ void node(int) {}
+    __device__ __forceinline__ void prim(int) {}
+};
+template <>
+struct Cnt<true> {
+    unsigned nodes[C_NQ], prims[C_NQ];
+    __device__ __forceinline__ Cnt() {
+        for (int i = 0; i < C_NQ; ++i) nodes[i] = prims[i] = 0u;
+    }
+    __device__ __forceinline__ void node(int q) { ++nodes[q]; }
+    __device__ __forceinline__ void prim(int q) { ++prims[q]; }
+};
+
+// ---------------------------------------------------------------------------
+// traversal stack in shared memory: entry i of this thread at base[i*stride]
+// ---------------------------------------------------------------------------
+struct Stack {
+    int2 *base;
+    int stride, cap;
+    unsigned int *guard;
+};
+__device__ __forceinline__ void spush(const Stack &s, int &sp, uint32_t ref, float key) {
+    if (sp < s.cap) {
+        s.base[sp * s.stride] = make_int2((int)ref, __float_as_int(key));
+        ++sp;
+    } else {
+        atomicOr(s.guard, 1u);  // overflow: recorded, entry dropped (no fault)
+    }
+}
+__device__ __forceinline__ void spop(const Stack &s, int &sp, uint32_t &ref, float &key) {
+    --sp;
+    int2 e = s.base[sp * s.stride];
+    ref = (uint32_t)e.x;
+    key = __int_as_float(e.y);
+}
+
+// ---------------------------------------------------------------------------
+// nodes
+// ---------------------------------------------------------------------------
+template <int D>
+struct Node {
+    float lo0[3], hi0[3], lo1[3], hi1[3];
+    uint32_t r0, r1;
+};
+template <int D>
+__device__ __forceinline__ Node<D> load_node(const float4 *nodes, uint32_t i) {
+    Node<D> n;
+    const float4 *q = nodes + 4 * (size_t)i;
+    float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    if constexpr (D == 2) {
+        n.lo0[0] = a.x; n.lo0[1] = a.y; n.hi0[0] = a.z; n.hi0[1] = a.w;
+        n.lo1[0] = b.x; n.lo1[1] = b.y; n.hi1[0] = b.z; n.hi1[1] = b.w;
+        n.lo0[2] = n.hi0[2] = n.lo1[2] = n.hi1[2] = 0.f;
+        n.r0 = __float_as_uint(c.x);
+        n.r1 = __float_as_uint(c.y);
+    } else {
+        float4 d = __ldg(q + 3);
+        n.lo0[0] = a.x; n.lo0[1] = a.y; n.lo0[2] = a.z; n.hi0[0] = a.w;
+        n.hi0[1] = b.x; n.hi0[2] = b.y; n.lo1[0] = b.z; n.lo1[1] = b.w;
+        n.lo1[2] = c.x; n.hi1[0] = c.y; n.hi1[1] = c.z; n.hi1[2] = c.w;
+        n.r0 = __float_as_uint(d.x);
+        n.r1 = __float_as_uint(d.y);
+    }
+    return n;
+}
+__device__ __forceinline__ bool is_leaf(uint32_t ref) { return (ref & WOST_LEAF_BIT) != 0u; }
+__device__ __forceinline__ uint32_t leaf_first(uint32_t ref) { return (ref & 0x7FFFFFFFu) >> 4; }
+__device__ __forceinline__ uint32_t leaf_count(uint32_t ref) { return (ref & 15u) + 1u; }
+
+template <int D>
+__device__ __forceinline__ float box_dist2(const float lo[3], const float hi[3], P3 x) {
+    float dx = fmaxf(fmaxf(lo[0] - x.x, x.x - hi[0]), 0.f);
+    float dy = fmaxf(fmaxf(lo[1] - x.y, x.y - hi[1]), 0.f);
+    float r = dx * dx + dy * dy;
+    if constexpr (D == 3) {
+        float dz = fmaxf(fmaxf(lo[2] - x.z, x.z - hi[2]), 0.f);
+        r += dz * dz;
+    }
+    return r;
+}
+
+// slab test: entry distance of the ray into the box, +inf if it misses [0, tmax]
+template <int D>
+__device__ __forceinline__ float box_ray(const float lo[3], const float hi[3], P3 o, P3 inv, float tmax) {
+    float t0x = (lo[0] - o.x) * inv.x, t1x = (hi[0] - o.x) * inv.x;
+    float t0y = (lo[1] - o.y) * inv.y, t1y = (hi[1] - o.y) * inv.y;
+    float tn = fmaxf(fminf(t0x, t1x), fminf(t0y, t1y));
+    float tf = fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y));
+    if constexpr (D == 3) {
+        float t0z = (lo[2] - o.z) * inv.z, t1z = (hi[2] - o.z) * inv.z;
+        tn = fmaxf(tn, fminf(t0z, t1z));
+        tf = fminf(tf, fmaxf(t0z, t1z));
+    }
+    tn = fmaxf(tn, 0.f);
+    tf = fminf(tf, tmax);
+    return tn <= tf ? tn : INFINITY;
+}
+
+// ---------------------------------------------------------------------------
+// primitives
+// ---------------------------------------------------------------------------
+template <int D>
+struct Prim {
+    P3 a, b, c;
+    float area;  // 3D only (stored); 2D computed when needed
+};
+template <int D>
+__device__ __forceinline__ Prim<D> load_prim(const float4 *prims, uint32_t k) {
+    Prim<D> p;
+    if constexpr (D == 2) {
+        float4 q = __ldg(prims + k);
+        p.a = mk(q.x, q.y, 0.f);
+        p.b = mk(q.z, q.w, 0.f);
+        p.c = p.b;
+        p.area = 0.f;
+    } else {
+        float4 q0 = __ldg(prims + 3 * (size_t)k), q1 = __ldg(prims + 3 * (size_t)k + 1),
+               q2 = __ldg(prims + 3 * (size_t)k + 2);
+        p.a = mk(q0.x, q0.y, q0.z);
+        p.b = mk(q1.x, q1.y, q1.z);
+        p.c = mk(q2.x, q2.y, q2.z);
+        p.area = q0.w;
+    }
+    return p;
+}
+
+// closest point on a segment: parameter t in [0,1]
+__device__ __forceinline__ float seg_param(P3 a, P3 b, P3 x, int dimz) {
+    P3 e = b - a, ap = x - a;
+    float ee = e.x * e.x + e.y * e.y + (dimz ? e.z * e.z : 0.f);
+    float t = (ap.x * e.x + ap.y * e.y + (dimz ? ap.z * e.z : 0.f)) / ee;
+    return fminf(fmaxf(t, 0.f), 1.f);
+}
+
+// closest point on triangle abc to p by Voronoi regions of the vertices,
+// edges and face (Ericson, Real-Time Collision Detection, 2005, Sec. 5.1.5);
+// returns barycentric weights of b and c in (v, w)
+__device__ __forceinline__ P3 tri_closest(P3 a, P3 b, P3 c, P3 p, float &v, float &w) {
+    P3 ab = b - a, ac = c - a, ap = p - a;
+    float d1 = dotp<3>(ab, ap), d2 = dotp<3>(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) { v = 0.f; w = 0.f; return a; }
+    P3 bp = p - b;
+    float d3 = dotp<3>(ab, bp), d4 = dotp<3>(ac, bp);
+    if (d3 >= 0.f && d4 <= d3) { v = 1.f; w = 0.f; return b; }
+    float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        float t = d1 / (d1 - d3);
+        v = t; w = 0.f;
+        return a + ab * t;
+    }
+    P3 cp = p - c;
+    float d5 = dotp<3>(ab, cp), d6 = dotp<3>(ac, cp);
+    if (d6 >= 0.f && d5 <= d6) { v = 0.f; w = 1.f; return c; }
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        float t = d2 / (d2 - d6);
+        v = 0.f; w = t;
+        return a + ac * t;
+    }
+    float va = d3 * d6 - d5 * d4;
+    if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+        float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        v = 1.f - t; w = t;
+        return b + (c - b) * t;
+    }
+    float den = 1.f / (va + vb + vc);
+    v = vb * den;
+    w = vc * den;
+    return a + ab * v + ac * w;
+}
+
+// closest point of a primitive: returns the point, squared distance and the
+// interpolation weights (2D: t along a->b in s0; 3D: weights of b, c)
+template <int D>
+__device__ __forceinline__ P3 prim_closest(const Prim<D> &p, P3 x, float &s0, float &s1) {
+    if constexpr (D == 2) {
+        float t = seg_param(p.a, p.b, x, 0);
+        s0 = t;
+        s1 = 0.f;
+        return p.a + (p.b - p.a) * t;
+    } else {
+        return tri_closest(p.a, p.b, p.c, x, s0, s1);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ P3 prim_normal(const Prim<D> &p) {
+    if constexpr (D == 2) {
+        P3 t = p.b - p.a;
+        float il = rsqrtf(t.x * t.x + t.y * t.y);
+        return mk(t.y * il, -t.x * il, 0.f);
+    } else {
+        P3 n = crossp(p.b - p.a, p.c - p.a);
+        return n * rsqrtf(dotp<3>(n, n));
+    }
+}
+template <int D>
+__device__ __forceinline__ float prim_area(const Prim<D> &p) {
+    if constexpr (D == 2) {
+        P3 t = p.b - p.a;
+        return sqrtf(t.x * t.x + t.y * t.y);
+    } else {
+        return p.area;
+    }
+}
+
+// ray o + t v against a primitive, 0 < t <= tmax
+template <int D>
+__device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tmax, float &t) {
+    if constexpr (D == 2) {
+        P3 e = p.b - p.a, ao = p.a - o;
+        float den = v.x * e.y - v.y * e.x;
+        if (den == 0.f) return false;
+        float inv = 1.f / den;
+        float tt = (ao.x * e.y - ao.y * e.x) * inv;
+        float u = (ao.x * v.y - ao.y * v.x) * inv;
+        if (u < 0.f || u > 1.f || !(tt > 0.f) || tt > tmax) return false;
+        t = tt;
+        return true;
+    } else {
+        P3 e1 = p.b - p.a, e2 = p.c - p.a;
+        P3 pv = crossp(v, e2);
+        float det = dotp<3>(e1, pv);
+        if (det == 0.f) return false;
+        float inv = 1.f / det;
+        P3 tv = o - p.a;
+        float u = dotp<3>(tv, pv) * inv;
+        if (u < 0.f || u > 1.f) return false;
+        P3 qv = crossp(tv, e1);
+        float w = dotp<3>(v, qv) * inv;
+        if (w < 0.f || u + w > 1.f) return false;
+        float tt = dotp<3>(e2, qv) * inv;
+        if (!(tt > 0.f) || tt > tmax) return false;
+        t = tt;
+        return true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Q.1 closest point on the Dirichlet boundary
+// ---------------------------------------------------------------------------
+struct Closest {
+    float d2;
+    int rec;
+    float s0, s1;
+    P3 p;
+};
+
+template <int D, bool CN = false>
+__device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &cnt) {
+    Closest best;
+    best.d2 = INFINITY;
+    best.rec = -1;
+    best.s0 = best.s1 = 0.f;
+    best.p = x;
+    if (T.root == WOST_EMPTY_REF) return best;
+    int sp = 0;
+    spush(st, sp, T.root, box_dist2<D>(T.root_lo, T.root_hi, x));
+    while (sp > 0) {
+        uint32_t ref;
+        float key;
+        spop(st, sp, ref, key);
+        if (key >= best.d2) continue;
+        if (is_leaf(ref)) {
+            uint32_t f = leaf_first(ref), c = leaf_count(ref);
+            for (uint32_t k = f; k < f + c; ++k) {
+                cnt.prim(C_Q1);
+                Prim<D> p = load_prim<D>(T.prims, k);
+                float s0, s1;
+                P3 q = prim_closest<D>(p, x, s0, s1);
+                P3 dq = q - x;
+                float d2 = dotp<D>(dq, dq);
+                if (d2 < best.d2) {
+                    best.d2 = d2;
+                    best.rec = (int)k;
+                    best.s0 = s0;
+                    best.s1 = s1;
+                    best.p = q;
+                }
+            }
+            continue;
+        }
+        cnt.node(C_Q1);
+        Node<D> n = load_node<D>(T.nodes, ref);
+        float d0 = box_dist2<D>(n.lo0, n.hi0, x), d1 = box_dist2<D>(n.lo1, n.hi1, x);
+        // push the farther child first so that the nearer one is popped next
+        if (d0 <= d1) {
+            if (d1 < best.d2) spush(st, sp, n.r1, d1);
+            if (d0 < best.d2) spush(st, sp, n.r0, d0);
+        } else {
+            if (d0 < best.d2) spush(st, sp, n.r0, d0);
+            if (d1 < best.d2) spush(st, sp, n.r1, d1);
+        }
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------------------
+// Q.2 closest visibility-silhouette point within rmax (Algs. 2-4)
+// ---------------------------------------------------------------------------
+// Alg. 4 HasSilhouette, conservative, without inverse trigonometry: the view
+// cone of the box (axis to its centre, half angle asin(rb/l)) and the normal
+// cone (axis a, half angle th) contain orthogonal directions iff the angle phi
+// between the axes satisfies |phi - pi/2| <= th + th_v, i.e. (when the sum is
+// below pi/2) |cos phi| <= sin(th + th_v).
+template <int D>
+__device__ __forceinline__ bool has_silhouette(const float lo[3], const float hi[3], float4 cone, P3 x) {
+    float ct = cone.w;
+    if (ct <= 0.f) return true;  // normal cone half angle >= 90 degrees
+    P3 c = mk(0.5f * (lo[0] + hi[0]), 0.5f * (lo[1] + hi[1]), 0.5f * (lo[2] + hi[2]));
+    P3 av = c - x;
+    float l2 = dotp<D>(av, av);
+    P3 ext = mk(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+    float rb2 = 0.25f * dotp<D>(ext, ext);
+    if (l2 <= rb2 * 1.0001f) return true;  // bounding sphere contains x
+    float il = rsqrtf(l2);
+    float sv = sqrtf(rb2) * il, cv = sqrtf(fmaxf(0.f, 1.f - sv * sv));
+    float st = sqrtf(fmaxf(0.f, 1.f - ct * ct));
+    float cos_sum = ct * cv - st * sv;
+    if (cos_sum <= 1e-6f) return true;  // combined half angle >= 90 degrees
+    float sin_sum = st * cv + ct * sv;
+    float cphi = (cone.x * av.x + cone.y * av.y + (D == 3 ? cone.z * av.z : 0.f)) * il;
+    return fabsf(cphi) <= sin_sum + 1e-5f;
+}
+
+template <int D>
+__device__ __forceinline__ float4 load_cone(const float4 *cones, uint32_t i, int which) {
+    return __ldg(cones + 2 * (size_t)i + which);
+}
+
+// silhouette candidate k: distance from x if it is a silhouette, else +inf
+template <int D>
+__device__ __forceinline__ float sil_test(const float4 *prims, uint32_t k, P3 x, float r2) {
+    P3 pe, n0, n1;
+    if constexpr (D == 2) {
+        float4 q0 = __ldg(prims + 2 * (size_t)k), q1 = __ldg(prims + 2 * (size_t)k + 1);
+        pe = mk(q0.x, q0.y, 0.f);
+        n0 = mk(q1.x, q1.y, 0.f);
+        n1 = mk(q1.z, q1.w, 0.f);
+    } else {
+        float4 q0 = __ldg(prims + 3 * (size_t)k), q1 = __ldg(prims + 3 * (size_t)k + 1),
+               q2 = __ldg(prims + 3 * (size_t)k + 2);
+        P3 a = mk(q0.x, q0.y, q0.z), b = mk(q1.x, q1.y, q1.z);
+        n0 = mk(q0.w, q1.w, q2.x);
+        n1 = mk(q2.y, q2.z, q2.w);
+        float t = seg_param(a, b, x, 1);
+        pe = a + (b - a) * t;
+    }
+    P3 v = pe - x;
+    float d2 = dotp<D>(v, v);
+    if (d2 >= r2) return INFINITY;
+    // Eq. SilhouetteDefinition; n1 = 0 for boundary vertices/edges
+    if (dotp<D>(v, n0) * dotp<D>(v, n1) <= 0.f) return d2;
+    return INFINITY;
+}
+
+template <int D, bool CN = false>
+__device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &st, Cnt<CN> &cnt) {
+    float r2 = rmax * rmax;
+    if (T.root == WOST_EMPTY_REF) return rmax;
+    int sp = 0;
+    float d0 = box_dist2<D>(T.root_lo, T.root_hi, x);
+    if (d0 >= r2) return rmax;
+    if (d0 > 0.f && !has_silhouette<D>(T.root_lo, T.root_hi, T.root_cone, x)) return rmax;
+    spush(st, sp, T.root, d0);
+    bool found = false;
+    while (sp > 0) {
+        uint32_t ref;
+        float key;
+        spop(st, sp, ref, key);
+        if (key >= r2) continue;
+        if (is_leaf(ref)) {
+            uint32_t f = leaf_first(ref), c = leaf_count(ref);
+            for (uint32_t k = f; k < f + c; ++k) {
+                cnt.prim(C_Q2);
+                float d2 = sil_test<D>(T.prims, k, x, r2);
+                if (d2 < r2) {
+                    r2 = d2;
+                    found = true;
+                }
+            }
+            continue;
+        }
+        cnt.node(C_Q2);
+        Node<D> n = load_node<D>(T.nodes, ref);
+        float e0 = box_dist2<D>(n.lo0, n.hi0, x), e1 = box_dist2<D>(n.lo1, n.hi1, x);
+        bool v0 = e0 < r2, v1 = e1 < r2;
+        if (v0 && e0 > 0.f) v0 = has_silhouette<D>(n.lo0, n.hi0, load_cone<D>(T.cones, ref, 0), x);
+        if (v1 && e1 > 0.f) v1 = has_silhouette<D>(n.lo1, n.hi1, load_cone<D>(T.cones, ref, 1), x);
+        if (e0 <= e1) {
+            if (v1) spush(st, sp, n.r1, e1);
+            if (v0) spush(st, sp, n.r0, e0);
+        } else {
+            if (v0) spush(st, sp, n.r0, e0);
+            if (v1) spush(st, sp, n.r1, e1);
+        }
+    }
+    return found ? sqrtf(r2) : rmax;
+}
+
+// ---------------------------------------------------------------------------
+// Q.3 ray against the Neumann boundary (closest hit / any hit)
+// ---------------------------------------------------------------------------
+template <int D, bool ANY, bool CN = false>
+__device__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, float &t_out, const Stack &st,
+                     Cnt<CN> &cnt) {
+    const int cq = ANY ? C_VIS : C_Q3;
+    int hit = -1;
+    if (T.root == WOST_EMPTY_REF) return -1;
+    P3 inv = mk(1.f / v.x, 1.f / v.y, D == 3 ? 1.f / v.z : 0.f);
+    float tb = tmax;
+    int sp = 0;
+    float t0 = box_ray<D>(T.root_lo, T.root_hi, o, inv, tb);
+    if (t0 == INFINITY) return -1;
+    spush(st, sp, T.root, t0);
+    while (sp > 0) {
+        uint32_t ref;
+        float key;
+        spop(st, sp, ref, key);
+        if (key > tb) continue;
+        if (is_leaf(ref)) {
+            uint32_t f = leaf_first(ref), c = leaf_count(ref);
+            for (uint32_t k = f; k < f + c; ++k) {
+                if ((int)k == skip) continue;
+                cnt.prim(cq);
+                Prim<D> p = load_prim<D>(T.prims, k);
+                float t;
+                if (prim_ray<D>(p, o, v, tb, t)) {
+                    tb = t;
+                    hit = (int)k;
+                    if (ANY) {
+                        t_out = tb;
+                        return hit;
+                    }
+                }
+            }
+            continue;
+        }
+        cnt.node(cq);
+        Node<D> n = load_node<D>(T.nodes, ref);
+        float a0 = box_ray<D>(n.lo0, n.hi0, o, inv, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, inv, tb);
+        if (a0 <= a1) {
+            if (a1 != INFINITY) spush(st, sp, n.r1, a1);
+            if (a0 != INFINITY) spush(st, sp, n.r0, a0);
+        } else {
+            if (a0 != INFINITY) spush(st, sp, n.r0, a0);
+            if (a1 != INFINITY) spush(st, sp, n.r1, a1);
+        }
+    }
+    t_out = tb;
+    return hit;
+}
+
+// ---------------------------------------------------------------------------
+// Q.4 hierarchical Neumann sample (Algs. 5-6)
+// ---------------------------------------------------------------------------
+struct NSample {
+    int rec;
+    float pdf;
+    P3 z;
+    float s0, s1;  // interpolation weights of z on the primitive
+};
+
+template <int D, bool CN = false>
+__device__ NSample q_sample(const TreeView &T, P3 x, float r, Stream &rng, Cnt<CN> &cnt) {
+    NSample out;
+    out.rec = -1;
+    out.pdf = 0.f;
+    out.z = x;
+    out.s0 = out.s1 = 0.f;
+    if (T.root == WOST_EMPTY_REF) return out;
+    float r2 = r * r;
+    if (box_dist2<D>(T.root_lo, T.root_hi, x) > r2) return out;
+    uint32_t ref = T.root;
+    float pdf = 1.f;
+    // Alg. 6: one random child among those whose box meets the ball, weighted
+    // by proximity of the box centre
+    while (!is_leaf(ref)) {
+        cnt.node(C_Q4);
+        Node<D> n = load_node<D>(T.nodes, ref);
+        float w0 = 0.f, w1 = 0.f;
+        if (box_dist2<D>(n.lo0, n.hi0, x) <= r2) {
+            P3 c = mk(0.5f * (n.lo0[0] + n.hi0[0]), 0.5f * (n.lo0[1] + n.hi0[1]), 0.5f * (n.lo0[2] + n.hi0[2]));
+            P3 dc = c - x;
+            w0 = rsqrtf(fmaxf(dotp<D>(dc, dc), 1e-24f));
+        }
+        if (box_dist2<D>(n.lo1, n.hi1, x) <= r2) {
+            P3 c = mk(0.5f * (n.lo1[0] + n.hi1[0]), 0.5f * (n.lo1[1] + n.hi1[1]), 0.5f * (n.lo1[2] + n.hi1[2]));
+            P3 dc = c - x;
+            w1 = rsqrtf(fmaxf(dotp<D>(dc, dc), 1e-24f));
+        }
+        float tot = w0 + w1;
+        if (!(tot > 0.f)) return out;
+        float p0 = w0 / tot;
+        if (rng.next() < p0) {
+            pdf *= p0;
+            ref = n.r0;
+        } else {
+            pdf *= 1.f - p0;
+            ref = n.r1;
+        }
+    }
+    // Alg. 6 leaf: reservoir choice proportional to area among primitives
+    // meeting the ball
+    uint32_t f = leaf_first(ref), c = leaf_count(ref);
+    float total = 0.f;
+    int chosen = -1;
+    Prim<D> cp;
+    for (uint32_t k = f; k < f + c; ++k) {
+        cnt.prim(C_Q4);
+        Prim<D> p = load_prim<D>(T.prims, k);
+        float s0, s1;
+        P3 q = prim_closest<D>(p, x, s0, s1);
+        P3 dq = q - x;
+        if (dotp<D>(dq, dq) <= r2) {
+            float A = prim_area<D>(p);
+            total += A;
+            if (rng.next() * total < A) {
+                chosen = (int)k;
+                cp = p;
+            }
+        }
+    }
+    if (chosen < 0) return out;
+    // Alg. 5: uniform point on the chosen primitive
+    if constexpr (D == 2) {
+        float u = rng.next();
+        out.z = cp.a + (cp.b - cp.a) * u;
+        out.s0 = u;
+        out.s1 = 0.f;
+        out.pdf = pdf / total;
+    } else {
+        float u1 = rng.next(), u2 = rng.next();
+        float su = sqrtf(u1);
+        float wb = su * (1.f - u2), wc = su * u2;
+        out.z = cp.a * (1.f - su) + cp.b * wb + cp.c * wc;
+        out.s0 = wb;
+        out.s1 = wc;
+        out.pdf = pdf / total;
+    }
+    out.rec = chosen;
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// exact solutions used as analytic boundary data (g = u, h = grad u . n,
+// f = -Lap u)
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ float fn_u(int fn, const float *p, P3 x) {
+    switch (fn) {
+    case 1: return expf(x.x) * cosf(x.y);
+    case 2: return sinf(2.f * x.x) * cosf(3.f * x.y);
+    case 3: return x.x * x.x - x.y * x.y + 0.5f * x.z;
+    case 4: return (1.f - (x.x * x.x + x.y * x.y + x.z * x.z)) / (2.f * D);
+    case 5: return p[0] + p[1] * x.x + p[2] * x.y + p[3] * x.z;
+    case 6: {
+        P3 d = x - mk(p[2], p[3], D == 3 ? p[4] : 0.f);
+        float rho = sqrtf(dotp<D>(d, d));
+        return D == 2 ? p[0] + p[1] * logf(rho) : p[0] + p[1] / rho;
+    }
+    default: return 0.f;
+    }
+}
+template <int D>
+__device__ __forceinline__ P3 fn_grad(int fn, const float *p, P3 x) {
+    switch (fn) {
+    case 1: {
+        float e = expf(x.x);
+        return mk(e * cosf(x.y), -e * sinf(x.y), 0.f);
+    }
+    case 2: return mk(2.f * cosf(2.f * x.x) * cosf(3.f * x.y), -3.f * sinf(2.f * x.x) * sinf(3.f * x.y), 0.f);
+    case 3: return mk(2.f * x.x, -2.f * x.y, 0.5f);
+    case 4: return x * (-1.f / D);
+    case 5: return mk(p[1], p[2], p[3]);
+    case 6: {
+        P3 d = x - mk(p[2], p[3], D == 3 ? p[4] : 0.f);
+        float rho2 = dotp<D>(d, d);
+        return D == 2 ? d * (p[1] / rho2) : d * (-p[1] / (rho2 * sqrtf(rho2)));
+    }
+    default: return mk(0.f, 0.f, 0.f);
+    }
+}
+template <int D>
+__device__ __forceinline__ float fn_neglap(int fn, P3 x) {
+    if (fn == 2) return 13.f * sinf(2.f * x.x) * cosf(3.f * x.y);
+    if (fn == 4) return 1.f;
+    return 0.f;
+}
+
+template <int D>
+__device__ __forceinline__ float corner_interp(const float4 *data, int rec, float s0, float s1) {
+    if constexpr (D == 2) {
+        float2 v = __ldg(reinterpret_cast<const float2 *>(data) + rec);
+        return v.x + (v.y - v.x) * s0;
+    } else {
+        float4 v = __ldg(data + rec);
+        return v.x * (1.f - s0 - s1) + v.y * s0 + v.z * s1;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float grid_eval(const FieldView &f, P3 y) {
+    float c[3] = {y.x, y.y, y.z};
+    int i0[3] = {0, 0, 0};
+    float fr[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int n = f.dims[a];
+        float g = (c[a] - f.origin[a]) / f.spacing[a];
+        g = fminf(fmaxf(g, 0.f), (float)(n - 1));
+        int i = min((int)floorf(g), max(n - 2, 0));
+        i0[a] = i;
+        fr[a] = n >= 2 ? g - (float)i : 0.f;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < (1 << D); ++m) {
+        float w = 1.f;
+        int idx[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int bit = (m >> a) & 1;
+            idx[a] = i0[a] + (f.dims[a] >= 2 ? bit : 0);
+            w *= bit ? fr[a] : 1.f - fr[a];
+        }
+        size_t lin = (size_t)idx[0] + (size_t)f.dims[0] * ((size_t)idx[1] + (D == 3 ? (size_t)f.dims[1] * idx[2] : 0));
+        acc += w * __ldg(f.grid + lin);
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// one walk
+// ---------------------------------------------------------------------------
+struct Walk {
+    P3 x, n;
+    float acc;
+    int steps;
+    bool onN, capped;
+    uint32_t point, index;
+};
+
+__device__ __forceinline__ float maxabs3(P3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+
+// One iteration of Alg. 1.  Returns true when the walk has terminated (its
+// estimate is then w.acc).
+template <int D, bool CN = false>
+__device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, const Stack &st, Cnt<CN> &cnt) {
+    // distance to the Dirichlet boundary (Q.1)
+    Closest cl = q_closest<D, CN>(sc.D, w.x, st, cnt);
+    w.steps += 1;
+    float dD = sqrtf(cl.d2);
+    if (dD < sp.epsilon || w.steps >= sp.max_steps) {
+        // epsilon shell: g at the closest point (R5: also at the step cap)
+        w.capped = !(dD < sp.epsilon);
+        if (cl.rec >= 0) {
+            float gv = sc.g.kind == FIELD_ANALYTIC ? fn_u<D>(sc.g.fn, sc.g.params, cl.p)
+                                                   : corner_interp<D>(sc.D.data, cl.rec, cl.s0, cl.s1);
+            w.acc += gv;
+        }
+        return true;
+    }
+    // R4: query origin off the Neumann boundary
+    float delta = sp.offset * (1.f + maxabs3(w.x));
+    P3 xq = w.onN ? w.x - w.n * delta : w.x;
+    // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
+    float dsil = q_silhouette<D, CN>(sc.S, xq, dD, st, cnt);
+    float r = fminf(dD, fmaxf(sp.r_min, dsil));
+    // direction: uniform, flipped into the hemisphere about -n_x on the boundary
+    uint32_t k = (uint32_t)(w.steps - 1);
+    uint4 rb = philox10(make_uint4(w.index, w.point, k, 0u), sp.key0, sp.key1);
+    P3 v;
+    if constexpr (D == 2) {
+        float s, c;
+        sincospif(2.f * u01(rb.x), &s, &c);
+        v = mk(c, s, 0.f);
+    } else {
+        float zc = 1.f - 2.f * u01(rb.x);
+        float rr = sqrtf(fmaxf(0.f, 1.f - zc * zc));
+        float s, c;
+        sincospif(2.f * u01(rb.y), &s, &c);
+        v = mk(rr * c, rr * s, zc);
+    }
+    if (w.onN && dotp<D>(w.n, v) > 0.f) v = v * -1.f;
+    // first hit with the Neumann part of the star boundary (Q.3)
+    float th;
+    int hrec = q_ray<D, false, CN>(sc.N, xq, v, r, -1, th, st, cnt);
+    P3 p, np = mk(0.f, 0.f, 0.f);
+    if (hrec >= 0) {
+        p = xq + v * th;
+        np = prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)hrec));
+    } else {
+        p = w.x + v * r;
+    }
+    // Neumann contribution from a separate sample z (Q.4) if h is present
+    float Nterm = 0.f;
+    bool hzero = sc.h.kind == FIELD_ANALYTIC && sc.h.fn == 0;
+    if (!hzero && sc.N.root != WOST_EMPTY_REF) {
+        Stream rng;
+        rng.init(sp.key0, sp.key1, w.index, w.point, k);
+        NSample zs = q_sample<D, CN>(sc.N, w.x, r, rng, cnt);
+        if (zs.rec >= 0 && zs.pdf > 0.f) {
+            P3 dz = zs.z - w.x;
+            float dzl = sqrtf(dotp<D>(dz, dz));
+            if (dzl < r) {
+                float tv;
+                int occ = q_ray<D, true, CN>(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, tv, st, cnt);
+                if (occ < 0) {
+                    float hv;
+                    if (sc.h.kind == FIELD_ANALYTIC) {
+                        P3 nz = prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)zs.rec));
+                        hv = dotp<D>(fn_grad<D>(sc.h.fn, sc.h.params, zs.z), nz);
+                    } else {
+                        hv = corner_interp<D>(sc.N.data, zs.rec, zs.s0, zs.s1);
+                    }
+                    float G = D == 2 ? logf(r / dzl) * (0.5f / 3.14159265358979f)
+                                     : (1.f / dzl - 1.f / r) * (0.25f / 3.14159265358979f);
+                    float alpha = w.onN ? 0.5f : 1.f;
+                    Nterm = G * hv / (alpha * zs.pdf);
+                }
+            }
+        }
+    }
+    // source contribution, reusing the direction v (Sec. 4.6)
+    float Sterm = 0.f;
+    if (sc.f.kind != FIELD_NONE) {
+        float ts;
+        if constexpr (D == 2) {
+            ts = r * sqrtf(u01(rb.y) * u01(rb.z));
+        } else {
+            ts = r * (0.5f + sinf(asinf(2.f * u01(rb.z) - 1.f) * (1.f / 3.f)));
+        }
+        P3 pd = p - w.x;
+        if (ts * ts < dotp<D>(pd, pd)) {
+            P3 y = w.x + v * ts;
+            float fv = sc.f.kind == FIELD_ANALYTIC ? fn_neglap<D>(sc.f.fn, y) : grid_eval<D>(sc.f, y);
+            Sterm = (D == 2 ? 0.25f : (1.f / 6.f)) * r * r * fv;
+        }
+    }
+    // R1: the step adds the Neumann and source terms
+    w.acc += Nterm + Sterm;
+    w.x = p;
+    w.n = np;
+    w.onN = hrec >= 0;
+    return false;
+}
+
+template <int D>
+__device__ __forceinline__ P3 load_point(const float *pts, int64_t i) {
+    if constexpr (D == 2) {
+        return mk(pts[2 * i], pts[2 * i + 1], 0.f);
+    } else {
+        return mk(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void walk_init(const SolveParams &sp, Walk &w, int64_t point, uint32_t index) {
+    w.x = load_point<D>(sp.points, point);
+    w.onN = sp.on_neumann ? sp.on_neumann[point] != 0 : false;
+    w.n = (w.onN && sp.normals) ? load_point<D>(sp.normals, point) : mk(0.f, 0.f, 0.f);
+    w.acc = 0.f;
+    w.steps = 0;
+    w.capped = false;
+    w.point = (uint32_t)point;
+    w.index = index;
+}
+
+}  // namespace wost

@@ -1,0 +1,98 @@
+// Internal data layout shared by the host scene builder and the CUDA kernels.
+//
+// Three binary hierarchies per scene, each flattened so that a node holds the
+// bounding boxes of BOTH children (one 64-byte fetch tests two boxes):
+//   D  BVH over the Dirichlet primitives     -> Q.1 closest point (Sec. 5)
+//   N  BVH over the Neumann primitives       -> Q.3 rays, Q.4 sampling (Sec. 5.2)
+//   S  normal-cone hierarchy over silhouette candidates of the Neumann part
+//      (2D: vertices, 3D: edges), each node also holding both children's
+//      normal cones                          -> Q.2 silhouette distance (Sec. 5.1)
+//
+// Node (64 B, float4 x4):
+//   2D: q0 = box0 (lo.x lo.y hi.x hi.y), q1 = box1, q2 = (ref0, ref1, -, -) as int bits
+//   3D: q0 = (b0.lo.x b0.lo.y b0.lo.z b0.hi.x), q1 = (b0.hi.y b0.hi.z b1.lo.x b1.lo.y),
+//       q2 = (b1.lo.z b1.hi.x b1.hi.y b1.hi.z), q3 = (ref0, ref1, -, -)
+// Child reference: bit 31 clear -> internal node index; set -> leaf with
+//   first primitive (bits 4..30) and count-1 (bits 0..3).
+// Cone record (S only, 32 B per node): float4 per child = (axis.xyz, cos(half angle));
+//   cos <= 0 means "may always contain a silhouette" (half angle >= 90 deg).
+//
+// Primitive records, in leaf order:
+//   D/N 2D: float4 (a.x a.y b.x b.y)
+//   D/N 3D: float4 x3: (a.xyz, area) (b.xyz, 0) (c.xyz, 0)
+//   S   2D: float4 x2: (p.x p.y 0 0) (n0.x n0.y n1.x n1.y)
+//   S   3D: float4 x3: (a.xyz n0.x) (b.xyz n0.y) (n0.z n1.xyz)
+//   A silhouette candidate with one adjacent Neumann primitive (a boundary
+//   vertex/edge, always a silhouette, Sec. 5.1) stores n1 = 0, so the
+//   predicate (v.n0)(v.n1) <= 0 holds for it without a flag.
+// Boundary data per primitive, in leaf order (corner values of g on D, h on N):
+//   2D float2, 3D float4 (xyz used).
+#pragma once
+
+#include <stdint.h>
+
+#define WOST_LEAF_BIT 0x80000000u
+#define WOST_EMPTY_REF 0xFFFFFFFFu
+#define WOST_MAX_LEAF 16
+#define WOST_MAX_DEPTH 60
+
+namespace wost {
+
+enum FieldKind { FIELD_NONE = 0, FIELD_CORNER = 2, FIELD_ANALYTIC = 3, FIELD_GRID = 4 };
+
+inline uint32_t leaf_ref(uint32_t first, uint32_t count) {
+    return WOST_LEAF_BIT | (first << 4) | (count - 1u);
+}
+
+struct FieldView {
+    int32_t kind;       // FieldKind (per-vertex data is converted to corners)
+    int32_t fn;         // analytic id
+    float params[8];
+    const float *grid;  // GRID values
+    float origin[3], spacing[3];
+    int32_t dims[3];
+};
+
+struct TreeView {
+    const float4 *nodes;    // 4 float4 per node
+    const float4 *cones;    // 2 float4 per node (S only)
+    const float4 *prims;    // records, see above
+    const float4 *data;     // D/N corner data (2D: reinterpret as float2)
+    const int32_t *ids;     // input index of each record
+    uint32_t root;          // child reference of the root (or WOST_EMPTY_REF)
+    float root_lo[3], root_hi[3];
+    float4 root_cone;       // S only
+    int32_t n_prims, n_nodes, depth;
+};
+
+struct SceneView {
+    int32_t dim;
+    TreeView D, N, S;
+    FieldView g, h, f;
+};
+
+struct SolveParams {
+    const float *points;        // device [n_points * dim]
+    const float *normals;       // device or null
+    const uint8_t *on_neumann;  // device or null
+    int64_t n_points;
+    int32_t walks_per_point;
+    uint32_t first_walk;
+    float epsilon, r_min;
+    int32_t max_steps;
+    uint32_t key0, key1;
+    float offset;               // relative ray-origin offset on the boundary
+    float vis_tmax;             // visibility ray end for the Neumann sample
+    int32_t stack_depth;        // shared-memory stack entries per thread
+};
+
+struct Accumulators {
+    double *sum, *sumsq;
+    unsigned long long *walks, *steps;
+    unsigned long long *capped;     // [1]
+    unsigned long long *next_walk;  // [1] work counter (persistent kernel)
+    unsigned int *guard;            // [1] guard flags
+    int *cancel;                    // [1] host-set cancel flag (mapped)
+};
+
+}  // namespace wost

@@ -1,0 +1,92 @@
+"""The C ABI without a GPU: the library builds, loads, exports every symbol
+that include/wost.h declares, and rejects malformed scenes on the host."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2302_11815_gb300 import build as libbuild
+from paper_2302_11815_gb300 import scenes, wost
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return wost.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "wost.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wost_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("wost_scene_create", "wost_scene_destroy", "wost_solve", "wost_poll", "wost_wait",
+                 "wost_cancel", "wost_solve_destroy", "wost_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll = C.CDLL(wost.LIBPATH)
+    missing = [n for n in declared_functions() if not hasattr(cdll, n)]
+    assert not missing, missing
+    assert wost.wost_abi_version() == 1
+
+
+def _good():
+    return scenes.disk_scene(16, "exp_cos", neumann=(np.arange(16) % 2).astype(np.uint8))
+
+
+@pytest.mark.parametrize("mutate, why", [
+    (lambda s: s.update(dim=4), "dim"),
+    (lambda s: s["prims"].__setitem__((3, 1), 999), "index out of range"),
+    (lambda s: s["prims"].__setitem__((2, 0), -1), "negative index"),
+    (lambda s: s["flags"].__setitem__(5, 2), "flag"),
+    (lambda s: s["vertices"].__setitem__((1, 0), np.nan), "non-finite"),
+    (lambda s: s.update(flags=np.ones(16, np.uint8)), "no Dirichlet"),
+    (lambda s: s.update(g={"kind": "per_vertex", "values": None}), "missing values"),
+    (lambda s: s.update(g={"kind": "analytic", "fn": "exp_cos", "params": []}, f={"kind": "per_vertex", "values": np.zeros(16)}), "f per vertex"),
+    (lambda s: s.update(h={"kind": "grid", "values": np.zeros(4), "origin": [0, 0], "spacing": [1, 1], "dims": [2, 2]}), "h grid"),
+])
+def test_malformed_scene_rejected_on_host(lib, mutate, why):
+    sc = _good()
+    sc["prims"] = sc["prims"].copy()
+    sc["vertices"] = sc["vertices"].copy()
+    sc["flags"] = sc["flags"].copy()
+    mutate(sc)
+    if sc["g"].get("values", 0) is None:
+        # a NULL values pointer with a PER_VERTEX kind
+        d = wost.wost_scene_desc()
+        V = np.ascontiguousarray(sc["vertices"], np.float32)
+        P = np.ascontiguousarray(sc["prims"], np.int32)
+        F = np.ascontiguousarray(sc["flags"], np.uint8)
+        d.dim, d.n_vertices, d.n_prims = 2, 16, 16
+        d.vertices = V.ctypes.data_as(C.POINTER(C.c_float))
+        d.prims = P.ctypes.data_as(C.POINTER(C.c_int32))
+        d.flags = F.ctypes.data_as(C.POINTER(C.c_uint8))
+        d.g.kind = wost.DATA["per_vertex"]
+        h = C.c_void_p()
+        st = lib.wost_scene_create(C.byref(d), C.byref(h))
+        assert st == wost.ERR_INVALID_ARG and not h.value
+        return
+    with pytest.raises(wost.WostError) as ei:
+        wost.wost_scene_create(sc)
+    assert ei.value.status == wost.ERR_INVALID_ARG, (why, str(ei.value))
+    assert wost.wost_last_error()
+
+
+def test_null_arguments(lib):
+    assert lib.wost_scene_create(None, None) == wost.ERR_INVALID_ARG
+    assert lib.wost_solve(None, None, None) == wost.ERR_INVALID_ARG
+    assert lib.wost_poll(None, None, None, None, None) == wost.ERR_INVALID_ARG
+    assert lib.wost_wait(None, 0.0) == wost.ERR_INVALID_ARG
+    assert lib.wost_cancel(None) == wost.ERR_INVALID_ARG
+    assert lib.wost_solve_destroy(None) == wost.ERR_INVALID_ARG
+    assert lib.wost_scene_destroy(None) == wost.ERR_INVALID_ARG
+    assert lib.wost_query_closest_dirichlet(None, 1, None, None, None, None, None) == wost.ERR_INVALID_ARG

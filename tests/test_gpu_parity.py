@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+and against exact solutions.
+
+Tolerances (FP32 walks and queries against FP64):
+  * query distances: |d_gpu - d_oracle| <= 1e-5 d + 4e-7 (relative 1e-5 with
+    an absolute floor of a few single-precision ulps at unit scale); the same
+    primitive except at ties;
+  * silhouette predicates and ray hits decided within float rounding of their
+    threshold may differ: at most 0.2% of the queries;
+  * walks: both sides draw the same Philox4x32-10 numbers, so per-point
+    estimates are strongly correlated; against the exact solution the
+    multiple-comparisons z test of statcheck.py; RMS error of the GPU at most
+    1.1x the oracle's at equal walk counts.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_11815_gb300 import scenes
+from statcheck import check_z
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ABS = 4e-7
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def wost():
+    from paper_2302_11815_gb300 import build as libbuild
+    from paper_2302_11815_gb300 import wost as w
+
+    assert torch.cuda.is_available()
+    libbuild.build()
+    w.load()
+    return w
+
+
+def _scenes():
+    return {
+        "flower": scenes.config1(),
+        "koch3": scenes.config2(grid=48, level=3),
+        "box_sphere": scenes.box_sphere_scene(m=6, n_lat=16, n_lon=32),
+        "cube_torus": scenes.config3(grid=24, nu=120, nv=48, cube_m=8),
+    }
+
+
+SCENES = _scenes()
+
+
+def _rand_points(sc, n, seed):
+    rng = np.random.default_rng(seed)
+    V = sc["vertices"]
+    lo, hi = V.min(0), V.max(0)
+    pad = 0.1 * (hi - lo)
+    return (lo - pad + (hi - lo + 2 * pad) * rng.random((n, sc["dim"]))).astype(np.float32)
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+# ---------------------------------------------------------------------------
+# queries
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", list(SCENES))
+def test_q1_closest_point_matches_brute_force(wost, name):
+    sc = SCENES[name]
+    S = wost.Scene(sc)
+    O = oracle.Scene(sc)
+    pts = _rand_points(sc, 20000, 1)
+    d, cl, pr = wost.wost_query_closest_dirichlet(S.handle, _dev(pts))
+    d, cl, pr = d.cpu().numpy(), cl.cpu().numpy(), pr.cpu().numpy()
+    od, ocl, opr = oracle.closest_dirichlet(O, pts.astype(np.float64))
+    assert np.all(np.abs(d - od) <= REL * od + ABS), np.max(np.abs(d - od) / (od + 1e-9))
+    assert np.all(np.abs(cl - ocl) <= 1e-5 + 1e-5 * np.abs(ocl))
+    diff = pr != opr
+    if diff.any():
+        # ties: the oracle's distance to the GPU's primitive equals the minimum
+        sub = {"dim": sc["dim"], "vertices": sc["vertices"], "prims": sc["prims"][pr[diff]],
+               "flags": np.zeros(diff.sum(), np.uint8), "g": {"kind": "none"}, "h": {"kind": "none"}}
+        for i, k in enumerate(np.nonzero(diff)[0]):
+            one = dict(sub, prims=sc["prims"][pr[k]][None], flags=np.zeros(1, np.uint8))
+            dk, _, _ = oracle.closest_dirichlet(oracle.Scene(one), pts[k:k + 1].astype(np.float64))
+            assert abs(dk[0] - od[k]) <= 1e-5 * od[k] + ABS
+            if i > 50:
+                break
+    S.close()
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_q2_silhouette_distance_matches_brute_force(wost, name):
+    sc = SCENES[name]
+    S = wost.Scene(sc)
+    O = oracle.Scene(sc)
+    pts = _rand_points(sc, 20000, 2)
+    od, _, _ = oracle.closest_dirichlet(O, pts.astype(np.float64))
+    rmax = np.minimum(od, 10.0).astype(np.float32)
+    d = wost.wost_query_silhouette(S.handle, _dev(pts), _dev(rmax)).cpu().numpy()
+    ods, _ = oracle.silhouette_distance(O, pts.astype(np.float64), rmax.astype(np.float64))
+    bad = np.abs(d - ods) > REL * ods + ABS
+    assert bad.mean() <= 2e-3, (bad.sum(), len(bad))
+    assert (ods < rmax).mean() > 0.05  # the test does see silhouettes
+    S.close()
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_q3_ray_hits_match_brute_force(wost, name):
+    sc = SCENES[name]
+    S = wost.Scene(sc)
+    O = oracle.Scene(sc)
+    rng = np.random.default_rng(3)
+    o = _rand_points(sc, 20000, 3)
+    v = rng.normal(size=o.shape).astype(np.float32)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    tmax = np.full(len(o), 0.6, np.float32)
+    hit, t, pr = (a.cpu().numpy() for a in wost.wost_query_intersect_neumann(S.handle, _dev(o), _dev(v), _dev(tmax)))
+    oh, ot, opr = oracle.intersect_neumann(O, o.astype(np.float64), v.astype(np.float64), tmax.astype(np.float64))
+    agree = (hit.astype(bool) == oh)
+    assert agree.mean() >= 1 - 2e-3
+    both = agree & oh
+    assert both.sum() > 100
+    assert np.mean(np.abs(t[both] - ot[both]) <= REL * ot[both] + ABS) >= 1 - 2e-3
+    assert np.mean(pr[both] == opr[both]) >= 1 - 2e-3
+    # skipping the primitive that was hit
+    sk = np.where(oh, opr, -1).astype(np.int32)
+    h2, t2, _ = (a.cpu().numpy() for a in wost.wost_query_intersect_neumann(
+        S.handle, _dev(o), _dev(v), _dev(tmax), skip=torch.from_numpy(sk).cuda()))
+    oh2, ot2, _ = oracle.intersect_neumann(O, o.astype(np.float64), v.astype(np.float64), tmax.astype(np.float64), skip=sk)
+    assert (h2.astype(bool) == oh2).mean() >= 1 - 2e-3
+    S.close()
+
+
+def test_q4_sampler_is_unbiased_on_gpu(wost):
+    # E[1{|z-x|<r}/pdf] = length (2D) or area (3D) of the Neumann boundary in
+    # the ball (Algs. 5-6 give an unbiased estimate for any tree)
+    k = 200
+    xs = np.linspace(-2, 2, k + 1)
+    V = np.c_[xs, np.zeros(k + 1)]
+    P = np.c_[np.arange(k), np.arange(1, k + 1)]
+    # one far Dirichlet segment (a scene needs one)
+    V = np.r_[V, [[-2, 5], [2, 5]]]
+    P = np.r_[P, [[k + 1, k + 2]]]
+    sc = {"dim": 2, "vertices": V.astype(np.float32), "prims": P.astype(np.int32),
+          "flags": np.r_[np.ones(k), 0].astype(np.uint8), "g": {"kind": "none"}, "h": {"kind": "none"},
+          "f": {"kind": "none"}}
+    S = wost.Scene(sc)
+    n = 200000
+    x = np.tile(np.array([[0.1, 0.3]], np.float32), (n, 1))
+    r = np.full(n, 0.5, np.float32)
+    z, pdf, pr = (a.cpu().numpy() for a in wost.wost_query_neumann_sample(S.handle, _dev(x), _dev(r), seed=5))
+    ok = (pr >= 0) & (pdf > 0) & (np.linalg.norm(z - x, axis=1) < 0.5)
+    vals = np.where(ok, 1.0 / np.where(pdf > 0, pdf, 1), 0.0)
+    want = 2 * np.sqrt(0.25 - 0.09)
+    assert abs(vals.mean() - want) < 4 * vals.std() / np.sqrt(n)
+    S.close()
+
+
+# ---------------------------------------------------------------------------
+# walks
+# ---------------------------------------------------------------------------
+def _gpu_solve(wost, sc, pts, walks, seed, kernel="plain", eps=None, max_steps=None, device_points=True):
+    S = wost.Scene(sc)
+    p = _dev(pts) if device_points else np.ascontiguousarray(pts, np.float32)
+    res = wost.solve(S, p, walks, eps or sc["epsilon"], sc.get("r_min", 0.0), max_steps or sc["max_steps"],
+                     seed=seed, kernel=kernel)
+    S.close()
+    return res
+
+
+def _allow(sc, eps):
+    fn, pr = sc["exact"]
+    L = np.max(np.linalg.norm(scenes.exact_grad(fn, pr, sc["vertices"].astype(float)), axis=1))
+    return eps * 1.05 * L
+
+
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_walk_config1_vs_exact_and_oracle(wost, kernel):
+    sc = scenes.config1()
+    pts = sc["points"]
+    res = _gpu_solve(wost, sc, pts, 512, 11, kernel)
+    assert res["done"] == 1 and int(res["walks"].sum()) == len(pts) * 512
+    assert res["capped_walks"] == 0 and res["guard_flags"] == 0
+    u = scenes.exact_u("exp_cos", (), pts)
+    check_z(res["mean"] - u, res["se"], _allow(sc, sc["epsilon"]), label="gpu")
+    ref = oracle.solve(oracle.Scene(sc), pts, 512, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=11)
+    rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
+    rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
+    assert rms_g <= 1.1 * rms_o, (rms_g, rms_o)
+    # same random streams: the GPU and oracle estimates track each other
+    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.2 * np.median(ref["se"])
+
+
+def test_walk_identical_streams_without_neumann_data(wost):
+    """With h = 0 the Neumann sampler cannot change an estimate, so the GPU
+    and the oracle follow the same walks: per-point means agree to float
+    rounding except where a float-vs-double decision splits a walk."""
+    sc = scenes.square_scene(8, fn="linear", params=(0.0, 0.0, 1.0, 0.0), neumann_sides=("left", "right"))
+    rng = np.random.default_rng(31)
+    pts = (0.05 + 0.9 * rng.random((128, 2))).astype(np.float32)
+    res = _gpu_solve(wost, sc, pts, 256, 5, eps=1e-3, max_steps=4096)
+    ref = oracle.solve(oracle.Scene(sc), pts, 256, 1e-3, None, 4096, seed=5)
+    d = np.abs(res["mean"] - ref["mean"])
+    assert np.median(d) < 1e-5, np.median(d)
+    assert np.mean(d < 1e-4) > 0.8
+    assert np.all(d < 4 * ref["se"] + 1e-4)
+
+
+def test_walk_koch_poisson_small_vs_exact_and_oracle(wost):
+    sc = scenes.config2(grid=16, level=3)
+    pts = sc["points"]
+    res = _gpu_solve(wost, sc, pts, 256, 21, "persistent")
+    u = scenes.exact_u("sin2x_cos3y", (), pts)
+    assert res["capped_walks"] <= 1e-3 * len(pts) * 256
+    check_z(res["mean"] - u, res["se"], _allow(sc, sc["epsilon"]), band=(0.4, 2.0), label="gpu koch")
+    ref = oracle.solve(oracle.Scene(sc), pts, 256, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=21)
+    rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
+    rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
+    assert rms_g <= 1.1 * rms_o, (rms_g, rms_o)
+
+
+def test_walk_3d_box_sphere_vs_exact_and_oracle(wost):
+    sc = scenes.box_sphere_scene()
+    rng = np.random.default_rng(25)
+    p = rng.uniform(-0.9, 0.9, (400, 3))
+    pts = p[np.linalg.norm(p, axis=1) > 0.5][:96].astype(np.float32)
+    res = _gpu_solve(wost, sc, pts, 512, 7, "persistent", eps=1e-3, max_steps=4096)
+    u = scenes.exact_u("quad3", (), pts)
+    check_z(res["mean"] - u, res["se"], _allow(sc, 1e-3), label="gpu 3d")
+    ref = oracle.solve(oracle.Scene(sc), pts, 512, 1e-3, None, 4096, seed=7)
+    rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
+    rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
+    assert rms_g <= 1.1 * rms_o, (rms_g, rms_o)
+
+
+def test_walk_source_term_bump_2d(wost):
+    sc = scenes.disk_scene(256, "bump", source=True)
+    rng = np.random.default_rng(4)
+    pts = scenes.ball_points(rng, 128, 2, 0.9)
+    res = _gpu_solve(wost, sc, pts, 1024, 3, eps=1e-3, max_steps=1024)
+    check_z(res["mean"] - scenes.exact_u("bump", (), pts), res["se"], _allow(sc, 1e-3), label="bump")
+
+
+def test_plain_and_persistent_give_the_same_walks(wost):
+    sc = scenes.config1(n_points=64)
+    a = _gpu_solve(wost, sc, sc["points"], 256, 9, "plain")
+    b = _gpu_solve(wost, sc, sc["points"], 256, 9, "persistent")
+    # identical walks; only the order of the FP64 additions differs
+    np.testing.assert_allclose(a["mean"], b["mean"], rtol=1e-9, atol=1e-12)
+    assert a["total_steps"] == b["total_steps"]
+
+
+def test_host_and_device_inputs_agree(wost):
+    sc = scenes.config1(n_points=32)
+    a = _gpu_solve(wost, sc, sc["points"], 64, 2, device_points=True)
+    b = _gpu_solve(wost, sc, sc["points"], 64, 2, device_points=False)
+    np.testing.assert_allclose(a["mean"], b["mean"], rtol=1e-9, atol=1e-12)
+
+
+def test_edge_cases(wost):
+    sc = scenes.config1(n_points=8)
+    # one point, one walk
+    r = _gpu_solve(wost, sc, sc["points"][:1], 1, 1)
+    assert r["walks"][0] == 1 and np.isfinite(r["mean"][0])
+    # step cap 1: every walk stops at once with g at the closest point
+    S = wost.Scene(sc)
+    r = wost.solve(S, _dev(sc["points"]), 16, 1e-3, 0.0, 1, seed=1)
+    assert r["capped_walks"] == 8 * 16
+    d, cl, _ = wost.wost_query_closest_dirichlet(S.handle, _dev(sc["points"]))
+    g = scenes.exact_u("exp_cos", (), cl.cpu().numpy())
+    np.testing.assert_allclose(r["mean"], g, rtol=1e-5, atol=1e-5)
+    # a point on the Dirichlet boundary ends immediately with g there
+    V = sc["vertices"]
+    on = ((V[0] + V[1]) / 2)[None].astype(np.float32)
+    r = wost.solve(S, _dev(on), 8, 1e-3, 0.0, 1024, seed=1)
+    assert r["total_steps"] == 8
+    np.testing.assert_allclose(r["mean"], scenes.exact_u("exp_cos", (), on), rtol=1e-5, atol=1e-5)
+    # pure Dirichlet scene (empty Neumann set) = walk on spheres
+    D = scenes.disk_scene(64, "exp_cos")
+    rng = np.random.default_rng(0)
+    pts = scenes.ball_points(rng, 32, 2, 0.8)
+    r = _gpu_solve(wost, D, pts, 512, 4, eps=1e-3, max_steps=1024)
+    check_z(r["mean"] - scenes.exact_u("exp_cos", (), pts), r["se"], _allow(D, 1e-3), label="wos")
+    # invalid solve arguments
+    for kw in (dict(walks=0), dict(eps=0.0), dict(rmin=1e-2), dict(steps=0)):
+        with pytest.raises(wost.WostError) as ei:
+            wost.wost_solve(S.handle, _dev(sc["points"]), kw.get("walks", 4), kw.get("eps", 1e-3),
+                            kw.get("rmin", 0.0), kw.get("steps", 16))
+        assert ei.value.status == wost.ERR_INVALID_ARG
+    S.close()
+
+
+def test_cancel_and_progressive_poll(wost):
+    sc = scenes.config2(grid=64, level=4)
+    S = wost.Scene(sc)
+    n = len(sc["points"])
+    h = wost.wost_solve(S.handle, _dev(sc["points"]), 4096, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=1,
+                        kernel="persistent")
+    m, se, wd, pr = wost.wost_poll(h, n)
+    assert pr["walks_done"] <= n * 4096
+    wost.wost_cancel(h)
+    with pytest.raises(wost.WostError) as ei:
+        wost.wost_wait(h, 120.0)
+    assert ei.value.status == wost.ERR_CANCELLED
+    m, se, wd, pr = wost.wost_poll(h, n)
+    assert pr["done"] == 1 and pr["walks_done"] < n * 4096
+    wost.wost_solve_destroy(h)
+    S.close()
