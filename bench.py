@@ -372,8 +372,194 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Workload 4: many scenes in one batched persistent launch against one
+    launch per scene (persistent and plain kernels).  The three forms run the
+    same walks (same seeds), so their RMS errors are equal by construction;
+    the line reports their times."""
+    import torch
+
+    from paper_2302_11815_gb300 import scenes, wost
+
+    wost.load()
+    t0 = time.perf_counter()
+    specs = scenes.config4(n_scenes=args.batch_scenes, points=(1, args.batch_max_points),
+                           walks=(16, args.batch_max_walks), max_scene=args.batch_max_prims)
+    gen_s = time.perf_counter() - t0
+    S = [wost.Scene(s) for s in specs]
+    pts = [torch.from_numpy(s["points"]).cuda() for s in specs]
+    reqs = [dict(points=p, walks_per_point=s["walks"], epsilon=s["epsilon"], r_min=s["r_min"],
+                 max_steps=s["max_steps"], seed=s["seed"]) for p, s in zip(pts, specs)]
+    stream = torch.cuda.Stream()
+
+    def batched():
+        hs = wost.wost_solve_batch([s.handle for s in S], reqs, stream=stream)
+        for h in hs:
+            wost.wost_wait(h)
+        out = [wost.wost_poll(h, len(s["points"])) for h, s in zip(hs, specs)]
+        for h in hs:
+            wost.wost_solve_destroy(h)
+        return out
+
+    def per_scene(kernel):
+        out = []
+        for s, sc, p in zip(S, specs, pts):
+            h = wost.wost_solve(s.handle, p, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"],
+                                seed=sc["seed"], kernel=kernel, stream=stream)
+            wost.wost_wait(h)
+            out.append(wost.wost_poll(h, len(sc["points"])))
+            wost.wost_solve_destroy(h)
+        return out
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = fn()
+        b.record(stream)
+        b.synchronize()
+        return res, a.elapsed_time(b) * 1e-3
+
+    batched()  # warm-up
+    rb, tb = timed(batched)
+    rp, tp = timed(lambda: per_scene("persistent"))
+    rq, tq = timed(lambda: per_scene("plain"))
+    steps = sum(r[3]["total_steps"] for r in rb)
+    walks = sum(r[3]["walks_done"] for r in rb)
+    maxdiff = max(float(np.max(np.abs(a[0] - b[0]) / (np.abs(b[0]) + 1e-9))) for a, b in zip(rb, rq))
+    err2 = ref2 = 0.0
+    for r, sc in zip(rb, specs):
+        u = scenes.exact_u(*sc["exact"], sc["points"])
+        err2 += float(np.sum((r[0] - u) ** 2))
+        ref2 += float(np.sum(u ** 2))
+    line = {"mode": "batch", "metric": "walk_steps_per_s", "unit": UNIT, "n_scenes": len(specs),
+            "dims": [s["dim"] for s in specs], "total_walks": int(walks), "total_steps": int(steps),
+            "total_points": int(sum(len(s["points"]) for s in specs)),
+            "batched": {"seconds": tb, "value": steps / tb, "launches": len({s["dim"] for s in specs})},
+            "per_scene_persistent": {"seconds": tp, "value": steps / tp, "launches": len(specs)},
+            "per_scene_plain": {"seconds": tq, "value": steps / tq, "launches": len(specs)},
+            "speedup_vs_plain": tq / tb, "rel_rms_error_all_forms": float(np.sqrt(err2 / ref2)),
+            "max_rel_diff_batched_vs_plain": maxdiff, "generation_seconds": gen_s,
+            "config": {"workload": "batched_64_scenes", "points_max": args.batch_max_points,
+                       "walks_max": args.batch_max_walks, "prims_max": args.batch_max_prims}}
+    print(json.dumps(line), flush=True)
+    for s in S:
+        s.close()
+    return 0
+
+
+def run_serve(args):
+    """Workload 5: resident 3D scenes, Poisson request stream into the
+    serving engine (continuous batching), latency percentiles and served
+    load."""
+    import threading
+
+    import torch
+
+    from paper_2302_11815_gb300 import scenes, wost
+
+    wost.load()
+    t0 = time.perf_counter()
+    specs = scenes.config5_scenes(total=args.serve_total_prims)
+    S = [wost.Scene(s) for s in specs]
+    reqs = scenes.config5_requests(duration_s=args.serve_seconds, rate=args.serve_rate,
+                                   points=(1e3, args.serve_max_points))
+    rng = np.random.default_rng(7)
+    pools = [[scenes.plane_points(rng, int(args.serve_max_points), s["tube"]) for _ in range(4)] for s in specs]
+    setup_s = time.perf_counter() - t0
+    eng = wost.wost_engine_create(round_seconds=args.round_seconds, max_walks_per_point=args.serve_walk_cap)
+    lock = threading.Lock()
+    live = []
+    done = []
+    stop = threading.Event()
+
+    def collector():
+        while not stop.is_set() or live:
+            with lock:
+                cur = list(live)
+            for item in cur:
+                h, rq, t_sub = item
+                try:
+                    wost.wost_wait(h, 0.0)
+                    ok = True
+                except wost.WostError as e:
+                    if e.status == wost.ERR_TIMEOUT:
+                        continue
+                    ok = False
+                m, se, wd, pr = wost.wost_poll(h, rq["n_points"])
+                wost.wost_solve_destroy(h)
+                with lock:
+                    live.remove(item)
+                    done.append({"latency": pr["elapsed_seconds"], "ok": ok, "n": rq["n_points"],
+                                 "walks": int(wd.min()), "se_max": float(se.max()), "target": rq["target_se"],
+                                 "steps": pr["total_steps"]})
+            time.sleep(0.001)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    start = time.perf_counter()
+    offered = 0
+    for rq in reqs:
+        wait = rq["t"] - (time.perf_counter() - start)
+        if wait > 0:
+            time.sleep(wait)
+        pool = pools[rq["scene"]][rq["seed"] % 4]
+        pts = pool[: rq["n_points"]]
+        sc = specs[rq["scene"]]
+        h = wost.wost_engine_submit(eng, S[rq["scene"]].handle, pts, rq["target_se"], 0, sc["epsilon"],
+                                    sc["r_min"], sc["max_steps"], seed=rq["seed"])
+        offered += 1
+        with lock:
+            live.append((h, rq, time.perf_counter()))
+    window = time.perf_counter() - start
+    drain_deadline = time.perf_counter() + args.serve_drain
+    while time.perf_counter() < drain_deadline:
+        with lock:
+            if not live:
+                break
+        time.sleep(0.05)
+    with lock:
+        for h, rq, _ in live:
+            wost.wost_cancel(h)
+    stop.set()
+    th.join(timeout=120)
+    stats = wost.wost_engine_get_stats(eng)
+    wost.wost_engine_destroy(eng)
+    total = time.perf_counter() - start
+    ok = [d for d in done if d["ok"]]
+    lat = np.array([d["latency"] for d in ok]) if ok else np.array([np.nan])
+    line = {"mode": "serve", "metric": "p99_latency_s", "unit": "s", "higher_is_better": False,
+            "p50_latency_s": float(np.nanpercentile(lat, 50)), "p99_latency_s": float(np.nanpercentile(lat, 99)),
+            "offered_requests": offered, "offered_rate": offered / max(window, 1e-9), "completed": len(ok),
+            "cancelled_at_end": len(done) - len(ok),
+            "served_points_per_s": sum(d["n"] for d in ok) / total,
+            "served_walk_steps_per_s": sum(d["steps"] for d in ok) / total,
+            "met_target": sum(1 for d in ok if d["se_max"] <= d["target"] * (1 + 1e-6)),
+            "capped": int(stats["capped"]), "engine": stats, "window_s": window, "total_s": total,
+            "setup_s": setup_s,
+            "config": {"workload": "serve_8_scenes", "scene_prims": [int(len(s["prims"])) for s in specs],
+                       "rate": args.serve_rate, "seconds": args.serve_seconds,
+                       "max_points": args.serve_max_points, "walk_cap": args.serve_walk_cap}}
+    print(json.dumps(line), flush=True)
+    for s in S:
+        s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve"])
+    ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--batch-max-points", type=float, default=1e5)
+    ap.add_argument("--batch-max-walks", type=float, default=1024)
+    ap.add_argument("--batch-max-prims", type=float, default=5e5)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-max-points", type=float, default=2.56e5)
+    ap.add_argument("--serve-total-prims", type=float, default=5e6)
+    ap.add_argument("--serve-walk-cap", type=int, default=65536)
+    ap.add_argument("--serve-drain", type=float, default=30.0)
+    ap.add_argument("--round-seconds", type=float, default=0.02)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -386,6 +572,10 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.mode == "batch":
+        sys.exit(run_batch(args))
+    if args.mode == "serve":
+        sys.exit(run_serve(args))
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))

@@ -180,6 +180,17 @@ typedef struct {
  * a null points array), OUT_OF_MEMORY, CUDA. */
 wost_status wost_solve(wost_scene *scene, const wost_solve_desc *desc, wost_solve_handle **out);
 
+/* Batching: starts n solves (any scenes of one device, any point counts, walk
+ * counts and parameters) in ONE persistent launch per dimension present (2D
+ * jobs and 3D jobs run in separate launches, back to back on the stream).
+ * Lanes take walks from a shared counter across all jobs, so uneven walk
+ * lengths do not idle the GPU.  out[i] (n handles) behaves like a handle from
+ * wost_solve; all of them complete together.  descs[i].kernel and block_size
+ * are taken from descs[0] (the counting kernel is not allowed here).
+ * Errors as for wost_solve; on error no handle is returned. */
+wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_solve_desc *descs, void *stream,
+                             wost_solve_handle **out);
+
 /* Snapshot of the running estimates.  mean and stderr_ (host, n_points each)
  * may be NULL.  stderr_ is sqrt(sample variance / walks); walks_done
  * (host, n_points, may be NULL) is the per-point walk count. */
@@ -206,6 +217,60 @@ wost_status wost_solve_device_accumulators(wost_solve_handle *solve, const doubl
  * Neumann sample; counts[5..9] the primitive tests of the same queries.
  * INVALID_ARG for a solve started with another kernel. */
 wost_status wost_solve_work_counts(wost_solve_handle *solve, uint64_t counts[10]);
+
+/* ---------------------------------------------------------------------- */
+/* Serving engine: continuous batching of solves with target errors.       */
+/* ---------------------------------------------------------------------- */
+/* A background scheduler owns one device stream.  Submitted requests wait
+ * in a FIFO until their state (points and FP64 accumulators) fits the
+ * engine's device-memory budget, then join the running mix: every
+ * scheduling round is one batched persistent launch over pieces (point
+ * ranges x walk ranges) of all active requests, sized to about
+ * round_seconds of GPU time, with up to two rounds queued so the GPU never
+ * waits for the host.  A request runs in stages of walks per point
+ * (min_walks, then growing from its own variance estimate); after each
+ * stage it completes if its largest per-point standard error is at most its
+ * target, or if it reached its walk cap.  A request's walks use its own
+ * seed and walk indices, so its result does not depend on what else runs
+ * (progressive estimates via wost_poll at any time).  This is the paper's
+ * progressive evaluation (Sec. 1) served to many clients. */
+typedef struct wost_engine wost_engine;
+
+typedef struct {
+    int32_t device;
+    int64_t memory_budget_bytes;  /* device bytes for request state; 0 = 1/4 of free memory */
+    double round_seconds;         /* target GPU time per round; 0 = 0.02 s                 */
+    int32_t min_walks;            /* walks per point of the first stage; 0 = 16           */
+    int32_t max_walks_per_point;  /* default walk cap; 0 = 65536                           */
+    int32_t block_size;           /* threads per block; 0 = 128                            */
+} wost_engine_desc;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, cancelled, rejected, capped;
+    int32_t queued, active;
+    uint64_t rounds;
+    double gpu_seconds;           /* summed GPU time of finished rounds          */
+    int64_t budget_bytes, used_bytes;
+    double round_budget_steps;    /* current walk-step budget of one round       */
+} wost_engine_stats;
+
+wost_status wost_engine_create(const wost_engine_desc *desc, wost_engine **out);
+
+/* Submits a request: desc as for wost_solve (points, seed, epsilon, r_min,
+ * max_steps; memory HOST or DEVICE; kernel, block_size and stream ignored);
+ * desc->walks_per_point is the request's walk cap (0 or larger than the
+ * engine's cap: the engine's cap).  target_se > 0: stop once every point's
+ * standard error is <= target_se; target_se == 0: run exactly the cap.
+ * Inputs are copied before return.  The handle works with wost_poll,
+ * wost_wait (CANCELLED for a cancelled request), wost_cancel and
+ * wost_solve_destroy.  Errors: INVALID_ARG; BUDGET if the request alone
+ * exceeds the memory budget (it could never be admitted). */
+wost_status wost_engine_submit(wost_engine *engine, wost_scene *scene, const wost_solve_desc *desc,
+                               double target_se, wost_solve_handle **out);
+wost_status wost_engine_get_stats(wost_engine *engine, wost_engine_stats *out);
+/* Cancels what is queued or running, waits for the device, joins the
+ * scheduler.  Handles of its requests stay valid until destroyed. */
+wost_status wost_engine_destroy(wost_engine *engine);
 
 /* ---------------------------------------------------------------------- */
 /* Batched geometric queries (Sec. 5, Q.1-Q.4), for checking and reuse.    */

@@ -1,0 +1,133 @@
+// Internal objects behind the C ABI handles, shared by wost_capi.cpp and
+// wost_engine.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/wost.h"
+#include "scene_build.h"
+#include "wost_kernels.h"
+
+namespace wost {
+
+// records the thread-local error message and returns s
+wost_status fail(wost_status s, const std::string &msg);
+wost_status cuda_fail(cudaError_t e, const char *what);
+#define CK(expr, what)                                     \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return wost::cuda_fail(_e, what); \
+    } while (0)
+
+// device allocation owned by a scene or solve
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n) {
+        bytes = n;
+        return n ? cudaMalloc(&p, n) : cudaSuccess;
+    }
+};
+
+template <class T>
+cudaError_t upload(DevBuf &b, const std::vector<T> &v) {
+    cudaError_t e = b.alloc(v.size() * sizeof(T));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// resources shared by the solves of one batched launch
+struct BatchShared {
+    DevBuf jobs[2], counters;  // counters: next walk (2D), next walk (3D), guard
+    unsigned long long total[2] = {0, 0};
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaStream_t own_stream = nullptr;
+    ~BatchShared() {
+        if (ev_done) cudaEventSynchronize(ev_done);
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_done) cudaEventDestroy(ev_done);
+        if (own_stream) cudaStreamDestroy(own_stream);
+    }
+};
+
+}  // namespace wost
+
+struct wost_engine;
+
+struct wost_scene {
+    int device = 0;
+    wost::HostScene host;
+    wost::SceneView view{};
+    wost::DevBuf bufs[16];
+    wost::DevBuf n_rec_of_id;
+    unsigned int *guard = nullptr;        // device guard word for query kernels
+    wost::SceneView *view_dev = nullptr;  // device copy of `view` (batched launches)
+    wost_scene_info info{};
+    int stack_depth = 0;
+    std::mutex mu;
+    ~wost_scene() {
+        if (guard) cudaFree(guard);
+        if (view_dev) cudaFree(view_dev);
+    }
+};
+
+struct wost_solve_handle {
+    wost_scene *scene = nullptr;
+    int device = 0;
+    int dim = 2;
+    int64_t n_points = 0;
+    int32_t walks = 0;
+    int block = 128;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t poll_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    bool own_events = false;
+    std::shared_ptr<wost::BatchShared> batch;  // set for solves started by wost_solve_batch
+    unsigned int *batch_guard = nullptr;
+    wost_engine *engine = nullptr;             // set for solves submitted to an engine
+    wost::SolveParams sp{};
+    wost::Accumulators acc{};
+    wost::DevBuf points, normals, onN;
+    wost::DevBuf sum, sumsq, walks_done, steps, globals;  // globals: capped, next_walk, guard
+    wost::DevBuf counts;                                   // counting kernel only
+    int kernel = 0;
+    int *cancel_host = nullptr;                            // mapped pinned
+    int *cancel_dev = nullptr;
+    std::chrono::steady_clock::time_point t_launch;
+    double elapsed_done = -1;
+    bool done = false;
+    wost_status final_status = WOST_OK;                    // engine requests
+    std::mutex mu;
+    ~wost_solve_handle() {
+        if (ev_done) cudaEventSynchronize(ev_done);
+        else if (stream) cudaStreamSynchronize(stream);
+        if (own_events && ev_start) cudaEventDestroy(ev_start);
+        if (own_events && ev_done) cudaEventDestroy(ev_done);
+        if (poll_stream) cudaStreamDestroy(poll_stream);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        if (cancel_host) cudaFreeHost(cancel_host);
+    }
+};
+
+namespace wost {
+// Validates a solve description, allocates and fills the solve's device
+// buffers on `stream`, fills h->sp and h->acc.  Does not launch.
+wost_status prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream, wost_solve_handle *h);
+// Blocks until the work queued so far on `stream` (the input copies) is done.
+wost_status wait_for_copies(cudaStream_t stream);
+// Engine side of wost_solve_destroy / wost_cancel for engine requests.
+void engine_detach(wost_engine *e, wost_solve_handle *h);
+}  // namespace wost

@@ -15,15 +15,13 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/wost.h"
-#include "scene_build.h"
-#include "wost_kernels.h"
+#include "capi_internal.h"
 
 using namespace wost;
 
-namespace {
+namespace wost {
 
-thread_local std::string g_last_error;
+static thread_local std::string g_last_error;
 
 wost_status fail(wost_status s, const std::string &msg) {
     g_last_error = msg;
@@ -33,78 +31,8 @@ wost_status cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? WOST_ERR_OUT_OF_MEMORY : WOST_ERR_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
-#define CK(expr, what)                              \
-    do {                                            \
-        cudaError_t _e = (expr);                    \
-        if (_e != cudaSuccess) return cuda_fail(_e, what); \
-    } while (0)
 
-// device allocation owned by a scene or solve
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    cudaError_t alloc(size_t n) {
-        bytes = n;
-        return n ? cudaMalloc(&p, n) : cudaSuccess;
-    }
-};
-
-template <class T>
-cudaError_t upload(DevBuf &b, const std::vector<T> &v) {
-    cudaError_t e = b.alloc(v.size() * sizeof(T));
-    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-    return e;
-}
-
-}  // namespace
-
-struct wost_scene {
-    int device = 0;
-    HostScene host;
-    SceneView view{};
-    DevBuf bufs[16];
-    DevBuf n_rec_of_id;
-    unsigned int *guard = nullptr;  // device guard word for query kernels
-    wost_scene_info info{};
-    int stack_depth = 0;
-    std::mutex mu;
-    ~wost_scene() {
-        if (guard) cudaFree(guard);
-    }
-};
-
-struct wost_solve_handle {
-    wost_scene *scene = nullptr;
-    int device = 0;
-    int dim = 2;
-    int64_t n_points = 0;
-    int32_t walks = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    cudaStream_t poll_stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    DevBuf points, normals, onN;
-    DevBuf sum, sumsq, walks_done, steps, globals;  // globals: capped, next_walk, guard
-    DevBuf counts;                                   // counting kernel only
-    int kernel = 0;
-    int *cancel_host = nullptr;                      // mapped pinned
-    int *cancel_dev = nullptr;
-    std::chrono::steady_clock::time_point t_launch;
-    double elapsed_done = -1;
-    bool done = false;
-    std::mutex mu;
-    ~wost_solve_handle() {
-        if (stream) cudaStreamSynchronize(stream);
-        if (ev_start) cudaEventDestroy(ev_start);
-        if (ev_done) cudaEventDestroy(ev_done);
-        if (poll_stream) cudaStreamDestroy(poll_stream);
-        if (own_stream && stream) cudaStreamDestroy(stream);
-        if (cancel_host) cudaFreeHost(cancel_host);
-    }
-};
+}  // namespace wost
 
 extern "C" {
 
@@ -168,6 +96,8 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         s->view.f = H.f;
         s->view.f.grid = (const float *)s->bufs[15].p;
         s->stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
+        CK(cudaMalloc(&s->view_dev, sizeof(SceneView)), "cudaMalloc view");
+        CK(cudaMemcpy(s->view_dev, &s->view, sizeof(SceneView), cudaMemcpyHostToDevice), "copy view");
         wost_scene_info &I = s->info;
         I.dim = H.dim;
         I.n_dirichlet = H.n_dirichlet;
@@ -208,114 +138,143 @@ wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out) {
     return WOST_OK;
 }
 
+}  // extern "C"
+
+// Validates a solve description, allocates and fills the solve's device
+// buffers on `stream`, and fills h->sp / h->acc.  Does not launch.
+wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream,
+                                 wost_solve_handle *h) {
+    if (!scene || !d) return fail(WOST_ERR_INVALID_ARG, "null argument");
+    if (d->n_points < 1 || !d->points) return fail(WOST_ERR_INVALID_ARG, "points missing");
+    if (d->n_points > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "more than 2^32-1 points");
+    if (d->walks_per_point < 1) return fail(WOST_ERR_INVALID_ARG, "walks_per_point must be >= 1");
+    if (!(d->epsilon > 0) || !std::isfinite(d->epsilon)) return fail(WOST_ERR_INVALID_ARG, "epsilon must be > 0");
+    float rmin = d->r_min == 0 ? d->epsilon : d->r_min;
+    if (!(rmin > 0) || rmin > d->epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
+    if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
+        return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
+    if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING)
+        return fail(WOST_ERR_INVALID_ARG, "unknown kernel");
+    int block = d->block_size ? d->block_size : 128;
+    if (block < 32 || block > 256 || block % 32)
+        return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
+    CK(cudaSetDevice(scene->device), "cudaSetDevice");
+    h->scene = scene;
+    h->device = scene->device;
+    h->dim = scene->view.dim;
+    h->n_points = d->n_points;
+    h->walks = d->walks_per_point;
+    h->kernel = d->kernel;
+    h->block = block;
+    h->stream = stream;
+    const int dim = h->dim;
+    CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    const size_t n = (size_t)d->n_points;
+    CK(h->points.alloc(n * dim * sizeof(float)), "cudaMalloc points");
+    cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, stream), "copy points");
+    if (d->normals && d->on_neumann) {
+        CK(h->normals.alloc(n * dim * sizeof(float)), "cudaMalloc normals");
+        CK(h->onN.alloc(n), "cudaMalloc on_neumann");
+        CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, stream), "copy normals");
+        CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, stream), "copy on_neumann");
+    }
+    CK(h->sum.alloc(n * 8), "cudaMalloc accumulators");
+    CK(h->sumsq.alloc(n * 8), "cudaMalloc accumulators");
+    CK(h->walks_done.alloc(n * 8), "cudaMalloc accumulators");
+    CK(h->steps.alloc(n * 8), "cudaMalloc accumulators");
+    CK(h->globals.alloc(4 * 8), "cudaMalloc accumulators");
+    CK(cudaMemsetAsync(h->sum.p, 0, n * 8, stream), "memset");
+    CK(cudaMemsetAsync(h->sumsq.p, 0, n * 8, stream), "memset");
+    CK(cudaMemsetAsync(h->walks_done.p, 0, n * 8, stream), "memset");
+    CK(cudaMemsetAsync(h->steps.p, 0, n * 8, stream), "memset");
+    CK(cudaMemsetAsync(h->globals.p, 0, 4 * 8, stream), "memset");
+    if (!h->cancel_host) {
+        CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+        *h->cancel_host = 0;
+        CK(cudaHostGetDevicePointer((void **)&h->cancel_dev, h->cancel_host, 0), "cudaHostGetDevicePointer");
+    }
+    SolveParams &sp = h->sp;
+    sp = SolveParams{};
+    sp.points = (const float *)h->points.p;
+    sp.normals = (const float *)h->normals.p;
+    sp.on_neumann = (const uint8_t *)h->onN.p;
+    sp.n_points = d->n_points;
+    sp.walks_per_point = d->walks_per_point;
+    sp.first_walk = d->first_walk;
+    sp.epsilon = d->epsilon;
+    sp.r_min = rmin;
+    sp.max_steps = d->max_steps;
+    sp.key0 = (uint32_t)d->seed;
+    sp.key1 = (uint32_t)(d->seed >> 32);
+    sp.offset = 1e-6f;
+    sp.vis_tmax = 1.f - 1e-4f;
+    sp.stack_depth = scene->stack_depth;
+    Accumulators &acc = h->acc;
+    acc = Accumulators{};
+    acc.sum = (double *)h->sum.p;
+    acc.sumsq = (double *)h->sumsq.p;
+    acc.walks = (unsigned long long *)h->walks_done.p;
+    acc.steps = (unsigned long long *)h->steps.p;
+    unsigned long long *g = (unsigned long long *)h->globals.p;
+    acc.capped = g;
+    acc.next_walk = g + 1;
+    acc.guard = (unsigned int *)(g + 2);
+    acc.cancel = h->cancel_dev;
+    return WOST_OK;
+}
+
+// The caller's arrays may be released once a solve call returns.
+wost_status wost::wait_for_copies(cudaStream_t stream) {
+    cudaEvent_t copied;
+    CK(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming), "cudaEventCreate");
+    cudaEventRecord(copied, stream);
+    cudaError_t ce = cudaEventSynchronize(copied);
+    cudaEventDestroy(copied);
+    if (ce != cudaSuccess) return cuda_fail(ce, "input copy");
+    return WOST_OK;
+}
+
+extern "C" {
+
 wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_handle **out) {
     try {
         if (!scene || !d || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
         *out = nullptr;
-        if (d->n_points < 1 || !d->points) return fail(WOST_ERR_INVALID_ARG, "points missing");
-        if (d->n_points > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "more than 2^32-1 points");
-        if (d->walks_per_point < 1) return fail(WOST_ERR_INVALID_ARG, "walks_per_point must be >= 1");
-        if (!(d->epsilon > 0) || !std::isfinite(d->epsilon)) return fail(WOST_ERR_INVALID_ARG, "epsilon must be > 0");
-        float rmin = d->r_min == 0 ? d->epsilon : d->r_min;
-        if (!(rmin > 0) || rmin > d->epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
-        if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
-        if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
-            return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
-        if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING)
-            return fail(WOST_ERR_INVALID_ARG, "unknown kernel");
-        int block = d->block_size ? d->block_size : 128;
-        if (block < 32 || block > 256 || block % 32) return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
         CK(cudaSetDevice(scene->device), "cudaSetDevice");
         std::unique_ptr<wost_solve_handle> h(new wost_solve_handle);
-        h->scene = scene;
-        h->device = scene->device;
-        h->dim = scene->view.dim;
-        h->n_points = d->n_points;
-        h->walks = d->walks_per_point;
-        h->kernel = d->kernel;
-        const int dim = h->dim;
-        if (d->stream) {
-            h->stream = (cudaStream_t)d->stream;
-        } else {
-            CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        cudaStream_t stream = (cudaStream_t)d->stream;
+        if (!stream) {
+            CK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "cudaStreamCreate");
             h->own_stream = true;
+            h->stream = stream;
         }
-        CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        wost_status st = prepare_solve(scene, d, stream, h.get());
+        if (st != WOST_OK) return st;
         CK(cudaEventCreate(&h->ev_start), "cudaEventCreate");
         CK(cudaEventCreate(&h->ev_done), "cudaEventCreate");
-        const size_t n = (size_t)d->n_points;
-        CK(h->points.alloc(n * dim * sizeof(float)), "cudaMalloc points");
-        cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, h->stream), "copy points");
-        if (d->normals && d->on_neumann) {
-            CK(h->normals.alloc(n * dim * sizeof(float)), "cudaMalloc normals");
-            CK(h->onN.alloc(n), "cudaMalloc on_neumann");
-            CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, h->stream), "copy normals");
-            CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, h->stream), "copy on_neumann");
-        }
-        CK(h->sum.alloc(n * 8), "cudaMalloc accumulators");
-        CK(h->sumsq.alloc(n * 8), "cudaMalloc accumulators");
-        CK(h->walks_done.alloc(n * 8), "cudaMalloc accumulators");
-        CK(h->steps.alloc(n * 8), "cudaMalloc accumulators");
-        CK(h->globals.alloc(4 * 8), "cudaMalloc accumulators");
-        CK(cudaMemsetAsync(h->sum.p, 0, n * 8, h->stream), "memset");
-        CK(cudaMemsetAsync(h->sumsq.p, 0, n * 8, h->stream), "memset");
-        CK(cudaMemsetAsync(h->walks_done.p, 0, n * 8, h->stream), "memset");
-        CK(cudaMemsetAsync(h->steps.p, 0, n * 8, h->stream), "memset");
-        CK(cudaMemsetAsync(h->globals.p, 0, 4 * 8, h->stream), "memset");
-        CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
-        *h->cancel_host = 0;
-        CK(cudaHostGetDevicePointer((void **)&h->cancel_dev, h->cancel_host, 0), "cudaHostGetDevicePointer");
-        // the caller's arrays may be released on return: wait for the copies
-        cudaEvent_t copied;
-        CK(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming), "cudaEventCreate");
-        cudaEventRecord(copied, h->stream);
-        cudaError_t ce = cudaEventSynchronize(copied);
-        cudaEventDestroy(copied);
-        if (ce != cudaSuccess) return cuda_fail(ce, "input copy");
-
-        SolveParams sp{};
-        sp.points = (const float *)h->points.p;
-        sp.normals = (const float *)h->normals.p;
-        sp.on_neumann = (const uint8_t *)h->onN.p;
-        sp.n_points = d->n_points;
-        sp.walks_per_point = d->walks_per_point;
-        sp.first_walk = d->first_walk;
-        sp.epsilon = d->epsilon;
-        sp.r_min = rmin;
-        sp.max_steps = d->max_steps;
-        sp.key0 = (uint32_t)d->seed;
-        sp.key1 = (uint32_t)(d->seed >> 32);
-        sp.offset = 1e-6f;
-        sp.vis_tmax = 1.f - 1e-4f;
-        sp.stack_depth = scene->stack_depth;
-        Accumulators acc{};
-        acc.sum = (double *)h->sum.p;
-        acc.sumsq = (double *)h->sumsq.p;
-        acc.walks = (unsigned long long *)h->walks_done.p;
-        acc.steps = (unsigned long long *)h->steps.p;
-        unsigned long long *g = (unsigned long long *)h->globals.p;
-        acc.capped = g;
-        acc.next_walk = g + 1;
-        acc.guard = (unsigned int *)(g + 2);
-        acc.cancel = h->cancel_dev;
+        h->own_events = true;
+        if ((st = wait_for_copies(stream)) != WOST_OK) return st;
+        const SolveParams &sp = h->sp;
+        const Accumulators &acc = h->acc;
         h->t_launch = std::chrono::steady_clock::now();
-        CK(cudaEventRecord(h->ev_start, h->stream), "cudaEventRecord");
+        CK(cudaEventRecord(h->ev_start, stream), "cudaEventRecord");
         cudaError_t le;
         if (d->kernel == WOST_KERNEL_PLAIN) {
-            le = launch_walk_plain(scene->view, sp, acc, block, h->stream);
+            le = launch_walk_plain(scene->view, sp, acc, h->block, stream);
         } else if (d->kernel == WOST_KERNEL_COUNTING) {
             le = h->counts.alloc(10 * 8);
-            if (le == cudaSuccess) le = cudaMemsetAsync(h->counts.p, 0, 10 * 8, h->stream);
+            if (le == cudaSuccess) le = cudaMemsetAsync(h->counts.p, 0, 10 * 8, stream);
             if (le == cudaSuccess)
-                le = launch_walk_count(scene->view, sp, acc, (unsigned long long *)h->counts.p, block, h->stream);
+                le = launch_walk_count(scene->view, sp, acc, (unsigned long long *)h->counts.p, h->block, stream);
         } else {
             int blocks = 0;
-            le = persistent_grid(dim, block, sp.stack_depth, &blocks);
-            if (le == cudaSuccess) le = launch_walk_persistent(scene->view, sp, acc, block, blocks, h->stream);
+            le = persistent_grid(h->dim, h->block, sp.stack_depth, &blocks);
+            if (le == cudaSuccess) le = launch_walk_persistent(scene->view, sp, acc, h->block, blocks, stream);
         }
         if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
-        CK(cudaEventRecord(h->ev_done, h->stream), "cudaEventRecord");
+        CK(cudaEventRecord(h->ev_done, stream), "cudaEventRecord");
         *out = h.release();
         return WOST_OK;
     } catch (const std::bad_alloc &) {
@@ -325,8 +284,91 @@ wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_h
     }
 }
 
+wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_solve_desc *descs, void *stream_arg,
+                             wost_solve_handle **out) {
+    try {
+        if (n < 1 || !scenes || !descs || !out) return fail(WOST_ERR_INVALID_ARG, "null argument or n < 1");
+        for (int32_t i = 0; i < n; ++i) {
+            out[i] = nullptr;
+            if (!scenes[i]) return fail(WOST_ERR_INVALID_ARG, "null scene");
+            if (scenes[i]->device != scenes[0]->device) return fail(WOST_ERR_INVALID_ARG, "scenes on different devices");
+        }
+        CK(cudaSetDevice(scenes[0]->device), "cudaSetDevice");
+        auto shared = std::make_shared<BatchShared>();
+        cudaStream_t stream = (cudaStream_t)stream_arg;
+        if (!stream) {
+            CK(cudaStreamCreateWithFlags(&shared->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            stream = shared->own_stream;
+        }
+        std::vector<std::unique_ptr<wost_solve_handle>> hs(n);
+        int block = descs[0].block_size ? descs[0].block_size : 128;
+        for (int32_t i = 0; i < n; ++i) {
+            hs[i].reset(new wost_solve_handle);
+            wost_solve_desc d = descs[i];
+            if (d.kernel == WOST_KERNEL_COUNTING) return fail(WOST_ERR_INVALID_ARG, "counting kernel in a batch");
+            d.block_size = block;
+            wost_status st = prepare_solve(scenes[i], &d, stream, hs[i].get());
+            if (st != WOST_OK) return st;
+            hs[i]->kernel = WOST_KERNEL_PERSISTENT;
+        }
+        // jobs per dimension, in the caller's order
+        std::vector<BatchJob> jobs[2];
+        int depth[2] = {0, 0};
+        for (int32_t i = 0; i < n; ++i) {
+            wost_solve_handle *h = hs[i].get();
+            int di = h->dim - 2;
+            BatchJob j;
+            j.scene = scenes[i]->view_dev;
+            j.sp = h->sp;
+            j.acc = h->acc;
+            j.walk_begin = shared->total[di];
+            shared->total[di] += (unsigned long long)h->n_points * (unsigned long long)h->walks;
+            depth[di] = std::max(depth[di], scenes[i]->stack_depth);
+            jobs[di].push_back(j);
+        }
+        for (int di = 0; di < 2; ++di) {
+            for (auto &j : jobs[di]) j.sp.stack_depth = depth[di];
+            CK(shared->jobs[di].alloc(jobs[di].size() * sizeof(BatchJob)), "cudaMalloc jobs");
+            if (!jobs[di].empty())
+                CK(cudaMemcpyAsync(shared->jobs[di].p, jobs[di].data(), jobs[di].size() * sizeof(BatchJob),
+                                   cudaMemcpyHostToDevice, stream), "copy jobs");
+        }
+        CK(shared->counters.alloc(4 * 8), "cudaMalloc counters");
+        CK(cudaMemsetAsync(shared->counters.p, 0, 4 * 8, stream), "memset");
+        CK(cudaEventCreate(&shared->ev_start), "cudaEventCreate");
+        CK(cudaEventCreate(&shared->ev_done), "cudaEventCreate");
+        wost_status st = wait_for_copies(stream);
+        if (st != WOST_OK) return st;
+        auto t0 = std::chrono::steady_clock::now();
+        CK(cudaEventRecord(shared->ev_start, stream), "cudaEventRecord");
+        unsigned long long *ctr = (unsigned long long *)shared->counters.p;
+        for (int di = 0; di < 2; ++di) {
+            if (jobs[di].empty()) continue;
+            int blocks = 0;
+            CK(batch_grid(di + 2, block, depth[di], &blocks), "occupancy");
+            CK(launch_walk_batch(di + 2, (const BatchJob *)shared->jobs[di].p, (int)jobs[di].size(), shared->total[di],
+                                 ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, stream),
+               "kernel launch");
+        }
+        CK(cudaEventRecord(shared->ev_done, stream), "cudaEventRecord");
+        for (int32_t i = 0; i < n; ++i) {
+            hs[i]->batch = shared;
+            hs[i]->ev_start = shared->ev_start;
+            hs[i]->ev_done = shared->ev_done;
+            hs[i]->t_launch = t0;
+            hs[i]->batch_guard = (unsigned int *)(ctr + 2);
+        }
+        for (int32_t i = 0; i < n; ++i) out[i] = hs[i].release();
+        return WOST_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WOST_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
 static wost_status check_done(wost_solve_handle *h) {
-    if (h->done) return WOST_OK;
+    if (h->done || !h->ev_done) return WOST_OK;  // engine requests are marked done by the engine
     cudaError_t q = cudaEventQuery(h->ev_done);
     if (q == cudaSuccess) {
         h->done = true;
@@ -348,6 +390,19 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
         if (st != WOST_OK) return st;
         bool was_done = h->done;
         const size_t n = (size_t)h->n_points;
+        if (!h->sum.p) {  // an engine request not admitted yet: nothing accumulated
+            for (size_t i = 0; i < n; ++i) {
+                if (mean) mean[i] = 0;
+                if (se) se[i] = 0;
+                if (walks_done) walks_done[i] = 0;
+            }
+            if (pr) {
+                std::memset(pr, 0, sizeof *pr);
+                pr->done = was_done ? 1 : 0;
+                pr->elapsed_seconds = h->elapsed_done > 0 ? h->elapsed_done : 0.0;
+            }
+            return WOST_OK;
+        }
         std::vector<double> s(n), q(n);
         std::vector<unsigned long long> w(n), stp(n), glob(4);
         CK(cudaMemcpyAsync(s.data(), h->sum.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
@@ -355,6 +410,9 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
         CK(cudaMemcpyAsync(w.data(), h->walks_done.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
         if (pr) CK(cudaMemcpyAsync(stp.data(), h->steps.p, n * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
         CK(cudaMemcpyAsync(glob.data(), h->globals.p, 4 * 8, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        unsigned int bg = 0;
+        if (h->batch_guard)
+            CK(cudaMemcpyAsync(&bg, h->batch_guard, sizeof bg, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
         CK(cudaStreamSynchronize(h->poll_stream), "poll sync");
         uint64_t tw = 0, ts = 0;
         for (size_t i = 0; i < n; ++i) {
@@ -374,11 +432,11 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
             pr->walks_done = tw;
             pr->total_steps = ts;
             pr->capped_walks = glob[0];
-            pr->guard_flags = (uint32_t)glob[2];
+            pr->guard_flags = (uint32_t)glob[2] | bg;
             pr->elapsed_seconds = was_done ? h->elapsed_done
                                            : std::chrono::duration<double>(std::chrono::steady_clock::now() - h->t_launch).count();
         }
-        if ((uint32_t)glob[2]) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+        if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
         return WOST_OK;
     } catch (const std::exception &e) {
         return fail(WOST_ERR_INTERNAL, e.what());
@@ -400,9 +458,16 @@ wost_status wost_wait(wost_solve_handle *h, double timeout_s) {
         if (timeout_s >= 0 && el >= timeout_s) return fail(WOST_ERR_TIMEOUT, "solve not finished");
         std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 20 : 500));
     }
+    if (h->engine || !h->ev_done) {  // engine request: its outcome was recorded by the engine
+        if (h->final_status == WOST_ERR_CANCELLED) return fail(WOST_ERR_CANCELLED, "solve was cancelled");
+        if (h->final_status != WOST_OK) return fail(h->final_status, "engine request failed");
+        return WOST_OK;
+    }
     unsigned long long glob[4];
     CK(cudaMemcpy(glob, h->globals.p, sizeof glob, cudaMemcpyDeviceToHost), "copy guard");
-    if ((uint32_t)glob[2]) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+    unsigned int bg = 0;
+    if (h->batch_guard) CK(cudaMemcpy(&bg, h->batch_guard, sizeof bg, cudaMemcpyDeviceToHost), "copy guard");
+    if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
     if (*(volatile int *)h->cancel_host) return fail(WOST_ERR_CANCELLED, "solve was cancelled");
     return WOST_OK;
 }
@@ -416,6 +481,7 @@ wost_status wost_cancel(wost_solve_handle *h) {
 wost_status wost_solve_destroy(wost_solve_handle *h) {
     if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
     cudaSetDevice(h->device);
+    if (h->engine) engine_detach(h->engine, h);  // waits until no round uses it
     delete h;
     return WOST_OK;
 }

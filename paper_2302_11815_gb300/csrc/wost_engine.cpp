@@ -1,0 +1,560 @@
+// Serving engine (include/wost.h, wost_engine_*): continuous batching of
+// walk-on-stars solves with target standard errors on one device.
+//
+// One scheduler thread per engine.  Each scheduling round is one batched
+// persistent launch (k_walk_batch, one per dimension present) over "pieces"
+// -- point ranges x walk ranges -- of every active request, sized so that a
+// round takes about round_seconds of GPU time (the walk-step budget adapts to
+// the measured round times).  Two rounds may be queued on the stream, so the
+// host prepares round k+1 while the GPU runs round k and the GPU never idles
+// between rounds.  Requests are admitted FIFO by device-memory budget, run in
+// stages of walks per point, and are checked after each stage with the
+// per-solve summary kernel (k_request_stats) on a second stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <thread>
+#include <unordered_map>
+
+#include "capi_internal.h"
+
+using namespace wost;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+    wost_solve_handle *h = nullptr;
+    wost_scene *scene = nullptr;
+    std::vector<float> pts, nrm;  // host copies of the inputs until admission
+    std::vector<uint8_t> onN;
+    wost_solve_desc desc{};
+    double target = 0;
+    int cap = 0;
+    int64_t bytes = 0;
+    Clock::time_point t_submit;
+    int stage_begin = 0, stage_end = 0;  // walks per point of the current stage
+    int64_t cursor = 0;                  // next point of the stage to issue
+    int outstanding = 0;                 // pieces in flight
+    double mean_steps = 64.0;            // running estimate of steps per walk
+    bool admitted = false, finished = false;
+};
+
+struct Piece {
+    Request *r;
+    int64_t p0, np;
+    int w0, nw;
+};
+
+struct Slot {
+    DevBuf jobs[2];
+    size_t cap[2] = {0, 0};
+    BatchJob *host = nullptr;  // pinned staging
+    size_t host_cap = 0;
+    DevBuf counters;           // next walk 2D, next walk 3D, guard
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool busy = false;
+};
+
+struct Round {
+    int slot;
+    std::vector<Piece> pieces;
+};
+
+}  // namespace
+
+struct wost_engine {
+    int device = 0;
+    cudaStream_t stream = nullptr, check_stream = nullptr;
+    int64_t budget = 0, used = 0;
+    double round_seconds = 0.02;
+    int min_walks = 16, cap = 65536, block = 128;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<Request *> pending;
+    std::vector<Request *> active;
+    std::unordered_map<wost_solve_handle *, Request *> by_handle;
+    std::deque<Round> inflight;
+    Slot slots[3];
+    double round_budget_steps = 4e6;
+    size_t rr = 0;
+    wost_engine_stats st{};
+    bool stop = false;
+    std::thread th;
+    DevBuf stat_jobs, stat_out;
+    StatJob *stat_host = nullptr;
+    size_t stat_cap = 0;
+};
+
+namespace {
+
+double since(Clock::time_point t) { return std::chrono::duration<double>(Clock::now() - t).count(); }
+
+void finish(wost_engine *e, Request *r, wost_status status) {
+    if (r->finished) return;
+    r->finished = true;
+    {
+        std::lock_guard<std::mutex> lk(r->h->mu);
+        r->h->done = true;
+        r->h->elapsed_done = since(r->t_submit);
+        r->h->final_status = status;
+    }
+    if (status == WOST_OK) e->st.completed++;
+    else if (status == WOST_ERR_CANCELLED) e->st.cancelled++;
+    e->active.erase(std::remove(e->active.begin(), e->active.end(), r), e->active.end());
+    e->done_cv.notify_all();
+}
+
+bool cancelled(const Request *r) { return *(volatile int *)r->h->cancel_host != 0; }
+
+void admit(wost_engine *e) {
+    while (!e->pending.empty()) {
+        Request *r = e->pending.front();
+        if (cancelled(r)) {
+            e->pending.pop_front();
+            finish(e, r, WOST_ERR_CANCELLED);
+            continue;
+        }
+        if (e->used + r->bytes > e->budget) break;  // FIFO: later requests wait too
+        e->pending.pop_front();
+        wost_status s;
+        {
+            std::lock_guard<std::mutex> hl(r->h->mu);  // pollers see either nothing or a complete state
+            s = prepare_solve(r->scene, &r->desc, e->stream, r->h);
+            r->h->stream = nullptr;  // the engine's stream is not the handle's to synchronize
+        }
+        r->pts.clear();
+        r->pts.shrink_to_fit();
+        r->nrm.clear();
+        r->nrm.shrink_to_fit();
+        r->onN.clear();
+        r->onN.shrink_to_fit();
+        if (s != WOST_OK) {
+            finish(e, r, s);
+            continue;
+        }
+        r->h->t_launch = Clock::now();
+        r->admitted = true;
+        e->used += r->bytes;
+        e->st.admitted++;
+        r->stage_begin = 0;
+        r->stage_end = std::min(r->cap, e->min_walks);
+        r->cursor = 0;
+        e->active.push_back(r);
+    }
+}
+
+// Stage checks of the requests whose current stage has fully completed.
+void check_stages(wost_engine *e, std::vector<Request *> &ready) {
+    if (ready.empty()) return;
+    size_t n = ready.size();
+    if (n > e->stat_cap) {
+        if (e->stat_host) cudaFreeHost(e->stat_host);
+        e->stat_cap = std::max<size_t>(n, 2 * e->stat_cap);
+        cudaMallocHost((void **)&e->stat_host, e->stat_cap * (sizeof(StatJob) + 32));
+        e->stat_jobs.~DevBuf();
+        new (&e->stat_jobs) DevBuf();
+        e->stat_out.~DevBuf();
+        new (&e->stat_out) DevBuf();
+        e->stat_jobs.alloc(e->stat_cap * sizeof(StatJob));
+        e->stat_out.alloc(e->stat_cap * 32);
+    }
+    int64_t maxn = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const Accumulators &a = ready[i]->h->acc;
+        e->stat_host[i] = StatJob{a.sum, a.sumsq, a.walks, a.steps, ready[i]->h->n_points};
+        maxn = std::max(maxn, ready[i]->h->n_points);
+    }
+    unsigned char *out = (unsigned char *)e->stat_out.p;
+    unsigned int *mvar = (unsigned int *)out;                                  // [n]
+    unsigned long long *minw = (unsigned long long *)(out + 8 * e->stat_cap);  // [n]
+    unsigned long long *ssum = minw + e->stat_cap, *wsum = ssum + e->stat_cap;
+    cudaMemcpyAsync(e->stat_jobs.p, e->stat_host, n * sizeof(StatJob), cudaMemcpyHostToDevice, e->check_stream);
+    cudaMemsetAsync(mvar, 0, n * 4, e->check_stream);
+    cudaMemsetAsync(minw, 0xFF, n * 8, e->check_stream);
+    cudaMemsetAsync(ssum, 0, n * 8, e->check_stream);
+    cudaMemsetAsync(wsum, 0, n * 8, e->check_stream);
+    launch_request_stats((const StatJob *)e->stat_jobs.p, (int)n, maxn, mvar, minw, ssum, wsum, e->check_stream);
+    std::vector<unsigned int> hv(n);
+    std::vector<unsigned long long> hs(n), hw(n);
+    cudaMemcpyAsync(hv.data(), mvar, n * 4, cudaMemcpyDeviceToHost, e->check_stream);
+    cudaMemcpyAsync(hs.data(), ssum, n * 8, cudaMemcpyDeviceToHost, e->check_stream);
+    cudaMemcpyAsync(hw.data(), wsum, n * 8, cudaMemcpyDeviceToHost, e->check_stream);
+    cudaError_t err = cudaStreamSynchronize(e->check_stream);
+    for (size_t i = 0; i < n; ++i) {
+        Request *r = ready[i];
+        if (err != cudaSuccess) {
+            finish(e, r, WOST_ERR_CUDA);
+            continue;
+        }
+        float mv;
+        std::memcpy(&mv, &hv[i], 4);
+        if (hw[i]) r->mean_steps = std::max(1.0, (double)hs[i] / (double)hw[i]);
+        int W = r->stage_end;
+        double t2 = r->target * r->target;
+        bool met = r->target > 0 && (double)mv <= t2 * W;
+        if (cancelled(r)) {
+            finish(e, r, WOST_ERR_CANCELLED);
+        } else if (met || W >= r->cap) {
+            if (!met && r->target > 0) e->st.capped++;
+            finish(e, r, WOST_OK);
+        } else {
+            double need = (double)mv / t2;
+            int next = (int)std::min<double>(r->cap, std::max(W + W / 2.0, std::ceil(1.05 * need / 16.0) * 16.0));
+            r->stage_begin = W;
+            r->stage_end = std::max(next, W + 1);
+            r->cursor = 0;
+        }
+    }
+}
+
+void retire_front(wost_engine *e) {
+    Round rd = std::move(e->inflight.front());
+    e->inflight.pop_front();
+    Slot &sl = e->slots[rd.slot];
+    float ms = 0;
+    cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
+    sl.busy = false;
+    e->st.rounds++;
+    e->st.gpu_seconds += ms * 1e-3;
+    if (ms > 0.05f) {
+        double f = std::min(2.0, std::max(0.5, e->round_seconds * 1e3 / ms));
+        e->round_budget_steps = std::min(2e10, std::max(1e5, e->round_budget_steps * f));
+    }
+    std::vector<Request *> ready;
+    e->done_cv.notify_all();
+    for (auto &p : rd.pieces) {
+        p.r->outstanding--;
+        if (!p.r->finished && p.r->outstanding == 0 && p.r->cursor >= p.r->h->n_points &&
+            std::find(ready.begin(), ready.end(), p.r) == ready.end())
+            ready.push_back(p.r);
+    }
+    check_stages(e, ready);
+}
+
+void process_cancels(wost_engine *e) {
+    std::vector<Request *> done;
+    for (Request *r : e->active)
+        if (!r->finished && r->outstanding == 0 && (cancelled(r) || e->stop)) done.push_back(r);
+    for (Request *r : done) finish(e, r, WOST_ERR_CANCELLED);
+}
+
+bool launch_round(wost_engine *e) {
+    int si = -1;
+    for (int i = 0; i < 3; ++i)
+        if (!e->slots[i].busy) {
+            si = i;
+            break;
+        }
+    if (si < 0) return false;
+    std::vector<Request *> iss;
+    for (Request *r : e->active)
+        if (!r->finished && r->cursor < r->h->n_points && !cancelled(r)) iss.push_back(r);
+    if (iss.empty()) return false;
+    Round rd;
+    rd.slot = si;
+    size_t n = iss.size();
+    size_t start = e->rr++ % n;
+    double remaining = e->round_budget_steps, share = remaining / (double)n;
+    for (int pass = 0; pass < 2 && remaining > 0; ++pass) {
+        for (size_t k = 0; k < n && remaining > 0; ++k) {
+            Request *r = iss[(start + k) % n];
+            int64_t left = r->h->n_points - r->cursor;
+            if (left <= 0) continue;
+            double cost = (double)(r->stage_end - r->stage_begin) * r->mean_steps;
+            double allow = pass == 0 ? share : remaining;
+            int64_t np = (int64_t)(allow / cost);
+            if (pass == 1 && np < 1) continue;
+            np = std::max<int64_t>(1, std::min(np, left));
+            rd.pieces.push_back(Piece{r, r->cursor, np, r->stage_begin, r->stage_end - r->stage_begin});
+            r->cursor += np;
+            r->outstanding++;
+            remaining -= (double)np * cost;
+        }
+    }
+    // job tables per dimension
+    Slot &sl = e->slots[si];
+    size_t np = rd.pieces.size();
+    if (np > sl.host_cap) {
+        if (sl.host) cudaFreeHost(sl.host);
+        sl.host_cap = std::max<size_t>(np, 2 * sl.host_cap);
+        if (cudaMallocHost((void **)&sl.host, sl.host_cap * sizeof(BatchJob)) != cudaSuccess) {
+            sl.host = nullptr;
+            sl.host_cap = 0;
+            for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_OUT_OF_MEMORY);
+            return false;
+        }
+    }
+    size_t cnt[2] = {0, 0};
+    int depth[2] = {0, 0};
+    for (auto &p : rd.pieces) {
+        int di = p.r->h->dim - 2;
+        cnt[di]++;
+        depth[di] = std::max(depth[di], p.r->scene->stack_depth);
+    }
+    size_t off[2] = {0, cnt[0]};
+    unsigned long long total[2] = {0, 0};
+    size_t fill[2] = {0, 0};
+    for (auto &p : rd.pieces) {
+        int di = p.r->h->dim - 2;
+        BatchJob j;
+        j.scene = p.r->scene->view_dev;
+        j.sp = p.r->h->sp;
+        j.sp.point_begin = p.p0;
+        j.sp.n_points = p.np;
+        j.sp.walks_per_point = p.nw;
+        j.sp.first_walk = p.r->h->sp.first_walk + (uint32_t)p.w0;
+        j.sp.stack_depth = depth[di];
+        j.acc = p.r->h->acc;
+        j.walk_begin = total[di];
+        total[di] += (unsigned long long)p.np * (unsigned long long)p.nw;
+        sl.host[off[di] + fill[di]++] = j;
+    }
+    if (!sl.counters.p) sl.counters.alloc(3 * 8);
+    cudaMemsetAsync(sl.counters.p, 0, 3 * 8, e->stream);
+    cudaEventRecord(sl.ev0, e->stream);
+    unsigned long long *ctr = (unsigned long long *)sl.counters.p;
+    cudaError_t err = cudaSuccess;
+    for (int di = 0; di < 2 && err == cudaSuccess; ++di) {
+        if (!cnt[di]) continue;
+        if (cnt[di] > sl.cap[di]) {
+            sl.jobs[di].~DevBuf();
+            new (&sl.jobs[di]) DevBuf();
+            sl.cap[di] = std::max<size_t>(cnt[di], 2 * sl.cap[di]);
+            err = sl.jobs[di].alloc(sl.cap[di] * sizeof(BatchJob));
+            if (err != cudaSuccess) break;
+        }
+        err = cudaMemcpyAsync(sl.jobs[di].p, sl.host + off[di], cnt[di] * sizeof(BatchJob), cudaMemcpyHostToDevice,
+                              e->stream);
+        int blocks = 0;
+        if (err == cudaSuccess) err = batch_grid(di + 2, e->block, depth[di], &blocks);
+        if (err == cudaSuccess)
+            err = launch_walk_batch(di + 2, (const BatchJob *)sl.jobs[di].p, (int)cnt[di], total[di], ctr + di,
+                                    (unsigned int *)(ctr + 2), depth[di], nullptr, e->block, blocks, e->stream);
+    }
+    cudaEventRecord(sl.ev1, e->stream);
+    if (err != cudaSuccess) {
+        for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_CUDA);
+        cudaStreamSynchronize(e->stream);
+        return false;
+    }
+    sl.busy = true;
+    e->inflight.push_back(std::move(rd));
+    return true;
+}
+
+void engine_loop(wost_engine *e) {
+    cudaSetDevice(e->device);
+    std::unique_lock<std::mutex> lk(e->mu);
+    for (;;) {
+        while (!e->inflight.empty() && cudaEventQuery(e->slots[e->inflight.front().slot].ev1) != cudaErrorNotReady)
+            retire_front(e);
+        process_cancels(e);
+        if (e->stop && e->inflight.empty()) break;
+        if (!e->stop) admit(e);
+        if (!e->stop && e->inflight.size() < 2 && launch_round(e)) continue;
+        if (!e->inflight.empty()) {
+            cudaEvent_t ev = e->slots[e->inflight.front().slot].ev1;
+            lk.unlock();
+            cudaEventSynchronize(ev);
+            lk.lock();
+        } else {
+            e->cv.wait_for(lk, std::chrono::milliseconds(2));
+        }
+    }
+    // stopped: whatever is left is cancelled
+    std::vector<Request *> left(e->active.begin(), e->active.end());
+    for (Request *r : left) finish(e, r, WOST_ERR_CANCELLED);
+    while (!e->pending.empty()) {
+        Request *r = e->pending.front();
+        e->pending.pop_front();
+        finish(e, r, WOST_ERR_CANCELLED);
+    }
+}
+
+}  // namespace
+
+namespace wost {
+
+void engine_detach(wost_engine *e, wost_solve_handle *h) {
+    std::unique_lock<std::mutex> lk(e->mu);
+    auto it = e->by_handle.find(h);
+    if (it == e->by_handle.end()) return;
+    Request *r = it->second;
+    if (!r->finished) {
+        *(volatile int *)h->cancel_host = 1;
+        e->cv.notify_all();
+    }
+    e->done_cv.wait(lk, [&] { return r->finished && r->outstanding == 0; });
+    if (r->admitted) e->used -= r->bytes;
+    e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), r), e->pending.end());
+    e->by_handle.erase(it);
+    delete r;
+    e->cv.notify_all();
+}
+
+}  // namespace wost
+
+extern "C" {
+
+wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
+    try {
+        if (!d || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+        *out = nullptr;
+        if (d->memory_budget_bytes < 0 || d->round_seconds < 0 || d->min_walks < 0 || d->max_walks_per_point < 0)
+            return fail(WOST_ERR_INVALID_ARG, "negative engine parameter");
+        int block = d->block_size ? d->block_size : 128;
+        if (block < 32 || block > 256 || block % 32) return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+        if (d->device < 0 || d->device >= ndev) return fail(WOST_ERR_INVALID_ARG, "device ordinal out of range");
+        CK(cudaSetDevice(d->device), "cudaSetDevice");
+        std::unique_ptr<wost_engine> e(new wost_engine);
+        e->device = d->device;
+        e->round_seconds = d->round_seconds > 0 ? d->round_seconds : 0.02;
+        e->min_walks = d->min_walks ? d->min_walks : 16;
+        e->cap = d->max_walks_per_point ? d->max_walks_per_point : 65536;
+        e->block = block;
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+        e->budget = d->memory_budget_bytes ? d->memory_budget_bytes : (int64_t)(fr / 4);
+        CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        CK(cudaStreamCreateWithFlags(&e->check_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (auto &s : e->slots) {
+            CK(cudaEventCreate(&s.ev0), "cudaEventCreate");
+            CK(cudaEventCreate(&s.ev1), "cudaEventCreate");
+        }
+        e->st.budget_bytes = e->budget;
+        wost_engine *raw = e.release();
+        raw->th = std::thread(engine_loop, raw);
+        *out = raw;
+        return WOST_OK;
+    } catch (const std::exception &ex) {
+        return fail(WOST_ERR_INTERNAL, ex.what());
+    }
+}
+
+wost_status wost_engine_submit(wost_engine *e, wost_scene *scene, const wost_solve_desc *d, double target_se,
+                               wost_solve_handle **out) {
+    try {
+        if (!e || !scene || !d || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+        *out = nullptr;
+        if (scene->device != e->device) return fail(WOST_ERR_INVALID_ARG, "scene on another device");
+        if (!(target_se >= 0) || !std::isfinite(target_se)) return fail(WOST_ERR_INVALID_ARG, "target_se must be >= 0");
+        if (d->n_points < 1 || !d->points) return fail(WOST_ERR_INVALID_ARG, "points missing");
+        if (d->n_points > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "more than 2^32-1 points");
+        if (d->walks_per_point < 0) return fail(WOST_ERR_INVALID_ARG, "walks_per_point must be >= 0");
+        if (!(d->epsilon > 0)) return fail(WOST_ERR_INVALID_ARG, "epsilon must be > 0");
+        float rmin = d->r_min == 0 ? d->epsilon : d->r_min;
+        if (!(rmin > 0) || rmin > d->epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
+        if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
+        if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
+            return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
+        const int dim = scene->view.dim;
+        const size_t n = (size_t)d->n_points;
+        std::unique_ptr<Request> r(new Request);
+        r->scene = scene;
+        r->target = target_se;
+        r->cap = (d->walks_per_point > 0 && d->walks_per_point < e->cap) ? d->walks_per_point : e->cap;
+        bool has_n = d->normals && d->on_neumann;
+        r->bytes = (int64_t)(n * (dim * 4 + 32 + (has_n ? dim * 4 + 1 : 0)) + 64);
+        if (r->bytes > e->budget) {
+            std::lock_guard<std::mutex> lk(e->mu);
+            e->st.rejected++;
+            return fail(WOST_ERR_BUDGET, "request exceeds the engine's memory budget");
+        }
+        CK(cudaSetDevice(e->device), "cudaSetDevice");
+        r->pts.resize(n * dim);
+        cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpy(r->pts.data(), d->points, n * dim * 4, kind), "copy points");
+        if (has_n) {
+            r->nrm.resize(n * dim);
+            r->onN.resize(n);
+            CK(cudaMemcpy(r->nrm.data(), d->normals, n * dim * 4, kind), "copy normals");
+            CK(cudaMemcpy(r->onN.data(), d->on_neumann, n, kind), "copy on_neumann");
+        }
+        r->desc = *d;
+        r->desc.points = r->pts.data();
+        r->desc.normals = has_n ? r->nrm.data() : nullptr;
+        r->desc.on_neumann = has_n ? r->onN.data() : nullptr;
+        r->desc.memory = WOST_MEM_HOST;
+        r->desc.walks_per_point = r->cap;
+        r->desc.kernel = WOST_KERNEL_PERSISTENT;
+        r->desc.block_size = e->block;
+        r->desc.stream = nullptr;
+        std::unique_ptr<wost_solve_handle> h(new wost_solve_handle);
+        h->engine = e;
+        h->scene = scene;
+        h->device = e->device;
+        h->dim = dim;
+        h->n_points = d->n_points;
+        h->walks = r->cap;
+        // the cancel flag exists before admission so that queued requests can be cancelled
+        CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
+        *h->cancel_host = 0;
+        CK(cudaHostGetDevicePointer((void **)&h->cancel_dev, h->cancel_host, 0), "cudaHostGetDevicePointer");
+        r->h = h.get();
+        r->t_submit = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            if (e->stop) return fail(WOST_ERR_CANCELLED, "engine is shutting down");
+            e->pending.push_back(r.get());
+            e->by_handle[h.get()] = r.get();
+            e->st.submitted++;
+        }
+        r.release();
+        e->cv.notify_all();
+        *out = h.release();
+        return WOST_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WOST_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (const std::exception &ex) {
+        return fail(WOST_ERR_INTERNAL, ex.what());
+    }
+}
+
+wost_status wost_engine_get_stats(wost_engine *e, wost_engine_stats *out) {
+    if (!e || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(e->mu);
+    *out = e->st;
+    out->queued = (int32_t)e->pending.size();
+    out->active = (int32_t)e->active.size();
+    out->budget_bytes = e->budget;
+    out->used_bytes = e->used;
+    out->round_budget_steps = e->round_budget_steps;
+    return WOST_OK;
+}
+
+wost_status wost_engine_destroy(wost_engine *e) {
+    if (!e) return fail(WOST_ERR_INVALID_ARG, "null engine");
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        e->stop = true;
+        for (auto &kv : e->by_handle) *(volatile int *)kv.first->cancel_host = 1;
+    }
+    e->cv.notify_all();
+    if (e->th.joinable()) e->th.join();
+    cudaSetDevice(e->device);
+    cudaStreamSynchronize(e->stream);
+    for (auto &kv : e->by_handle) {
+        kv.first->engine = nullptr;  // the handle outlives the engine
+        delete kv.second;
+    }
+    e->by_handle.clear();
+    for (auto &s : e->slots) {
+        if (s.host) cudaFreeHost(s.host);
+        if (s.ev0) cudaEventDestroy(s.ev0);
+        if (s.ev1) cudaEventDestroy(s.ev1);
+    }
+    if (e->stat_host) cudaFreeHost(e->stat_host);
+    cudaStreamDestroy(e->check_stream);
+    cudaStreamDestroy(e->stream);
+    delete e;
+    return WOST_OK;
+}
+
+}  // extern "C"

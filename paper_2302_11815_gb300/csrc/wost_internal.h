@@ -75,7 +75,8 @@ struct SolveParams {
     const float *points;        // device [n_points * dim]
     const float *normals;       // device or null
     const uint8_t *on_neumann;  // device or null
-    int64_t n_points;
+    int64_t point_begin;        // first point of this launch/job (batched rounds)
+    int64_t n_points;           // points [point_begin, point_begin + n_points)
     int32_t walks_per_point;
     uint32_t first_walk;
     float epsilon, r_min;
@@ -93,6 +94,22 @@ struct Accumulators {
     unsigned long long *next_walk;  // [1] work counter (persistent kernel)
     unsigned int *guard;            // [1] guard flags
     int *cancel;                    // [1] host-set cancel flag (mapped)
+};
+
+// Accumulators of one solve, for the per-solve summary kernel.
+struct StatJob {
+    const double *sum, *sumsq;
+    const unsigned long long *walks, *steps;
+    int64_t n;
+};
+
+// One entry of a batched launch: a solve's walks [walk_begin, walk_begin +
+// n_points * walks_per_point) in the launch's walk index space.
+struct BatchJob {
+    const SceneView *scene;         // device copy of the scene's view
+    SolveParams sp;
+    Accumulators acc;
+    unsigned long long walk_begin;
 };
 
 }  // namespace wost

@@ -13,6 +13,8 @@
 // accesses fall in distinct banks.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "wost_device.cuh"
 #include "wost_kernels.h"
 
@@ -117,6 +119,111 @@ __global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, con
             have = false;
         }
     }
+}
+
+// Batched persistent kernel: many solves (scenes, point sets, walk counts,
+// parameters) in one launch.  The walk index space is the concatenation of
+// the jobs' walks; a lane maps its next index to a job by binary search over
+// the jobs' first indices and runs that job's walk on that job's scene.
+template <int D>
+__global__ void __launch_bounds__(256) k_walk_batch(const BatchJob *__restrict__ jobs, int n_jobs,
+                                                    unsigned long long total, unsigned long long *counter,
+                                                    unsigned int *guard, int stack_depth, const int *cancel) {
+    Stack st = make_stack(stack_depth, guard);
+    const int lane = threadIdx.x & 31;
+    Walk w;
+    int job = -1;
+    for (;;) {
+        unsigned act = __activemask();
+        unsigned need = __ballot_sync(act, job < 0);
+        if (need) {
+            int lead = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == lead) {
+                bool stop = cancel && *(volatile const int *)cancel != 0;
+                base = stop ? total : atomicAdd(counter, (unsigned long long)__popc(need));
+            }
+            base = __shfl_sync(act, base, lead);
+            if (job < 0) {
+                unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+                if (my < total) {
+                    int lo = 0, hi = n_jobs - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (jobs[mid].walk_begin <= my) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    job = lo;
+                    if (*(volatile const int *)jobs[job].acc.cancel != 0) {
+                        job = -1;  // cancelled solve: its remaining walks are skipped
+                        continue;
+                    }
+                    const SolveParams &sp = jobs[job].sp;
+                    unsigned long long local = my - jobs[job].walk_begin;
+                    int64_t pt = sp.point_begin + (int64_t)(local / (uint64_t)sp.walks_per_point);
+                    uint32_t j = (uint32_t)(local % (uint64_t)sp.walks_per_point) + sp.first_walk;
+                    walk_init<D>(sp, w, pt, j);
+                }
+            }
+        }
+        if (job < 0) break;
+        Cnt<false> cnt;
+        if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, st, cnt)) {
+            accumulate(jobs[job].acc, w);
+            job = -1;
+        }
+    }
+}
+
+// Per-solve summary of the FP64 accumulators (serving engine): largest
+// per-point sample variance, smallest per-point walk count, and the sums of
+// steps and walks.  grid.y = solve, grid.x strides over points.
+__global__ void k_request_stats(const StatJob *jobs, int n_jobs, unsigned int *max_var_bits,
+                                unsigned long long *min_walks, unsigned long long *steps_sum,
+                                unsigned long long *walks_sum) {
+    int j = blockIdx.y;
+    if (j >= n_jobs) return;
+    const StatJob J = jobs[j];
+    float mv = 0.f;
+    unsigned long long mw = ~0ull, ss = 0, ws = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long w = J.walks[i];
+        double c = (double)w;
+        float var = 3.0e38f;
+        if (w > 1) {
+            double m = J.sum[i] / c;
+            var = (float)fmax(0.0, (J.sumsq[i] - c * m * m) / (c - 1.0));
+        }
+        mv = fmaxf(mv, var);
+        mw = w < mw ? w : mw;
+        ss += J.steps[i];
+        ws += w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mv = fmaxf(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, mw, o);
+        mw = t < mw ? t : mw;
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(max_var_bits + j, __float_as_uint(mv));  // non-negative floats order like their bits
+        atomicMin(min_walks + j, mw);
+        atomicAdd(steps_sum + j, ss);
+        atomicAdd(walks_sum + j, ws);
+    }
+}
+
+cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_points, unsigned int *max_var_bits,
+                                 unsigned long long *min_walks, unsigned long long *steps_sum,
+                                 unsigned long long *walks_sum, cudaStream_t s) {
+    if (n_jobs <= 0) return cudaSuccess;
+    const int block = 256;
+    int gx = (int)std::min<int64_t>((max_points + block - 1) / block, 128);
+    dim3 grid(gx > 0 ? gx : 1, n_jobs);
+    k_request_stats<<<grid, block, 0, s>>>(jobs, n_jobs, max_var_bits, min_walks, steps_sum, walks_sum);
+    return cudaGetLastError();
 }
 
 // Counting variant of the plain kernel: same walks, plus per-query node
@@ -247,6 +354,33 @@ cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const 
         k_walk_count<2><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, stats);
     else
         k_walk_count<3><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t sm = smem_bytes(depth, block);
+    if (e == cudaSuccess && sm > 48 * 1024)
+        e = dim == 2 ? cudaFuncSetAttribute(k_walk_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                     : cudaFuncSetAttribute(k_walk_batch<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<2>, block, sm)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<3>, block, sm);
+    if (e != cudaSuccess) return e;
+    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_walk_batch(int dim, const BatchJob *jobs, int n_jobs, unsigned long long total,
+                              unsigned long long *counter, unsigned int *guard, int depth, const int *cancel,
+                              int block, int blocks, cudaStream_t s) {
+    size_t sm = smem_bytes(depth, block);
+    if (dim == 2)
+        k_walk_batch<2><<<blocks, block, sm, s>>>(jobs, n_jobs, total, counter, guard, depth, cancel);
+    else
+        k_walk_batch<3><<<blocks, block, sm, s>>>(jobs, n_jobs, total, counter, guard, depth, cancel);
     return cudaGetLastError();
 }
 

@@ -562,3 +562,146 @@ def ball_points(rng, n, dim, radius):
     x /= np.linalg.norm(x, axis=1, keepdims=True)
     r = radius * rng.random(n) ** (1.0 / dim)
     return (x * r[:, None]).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Workload 4: many scenes of uneven size, point count and walk count
+# ---------------------------------------------------------------------------
+def radial_polygon(n, rng, base=1.0, amp=0.25, lobes=5, rough=0.03):
+    th = 2 * np.pi * np.arange(n) / n
+    k = np.arange(1, 9)
+    ph = rng.uniform(0, 2 * np.pi, len(k))
+    noise = np.sum(np.sin(np.outer(th, k) + ph) / k, 1)
+    r = base * (1 + amp * np.sin(lobes * th) + rough * noise / 2.7)
+    return np.stack([r * np.cos(th), r * np.sin(th)], 1)
+
+
+def batched_scene(i, n_prims, dim, d_frac, n_points, walks, seed):
+    """One scene of the batched workload: about n_prims primitives, a
+    contiguous Dirichlet fraction d_frac, n_points evaluation points."""
+    rng = np.random.default_rng(seed)
+    if dim == 2:
+        n_hole = max(16, n_prims // 4)
+        n_out = max(32, n_prims - n_hole)
+        outer = radial_polygon(n_out, rng)
+        hole = random_walk_hole(rng, n_hole, base=0.3, lo=0.2, hi=0.4, sigma=0.5 / np.sqrt(n_hole))
+        seg = np.linalg.norm(np.roll(outer, -1, axis=0) - outer, axis=1)
+        arc = np.cumsum(seg) - 0.5 * seg
+        total = seg.sum() + np.linalg.norm(np.roll(hole, -1, axis=0) - hole, axis=1).sum()
+        oflags = (arc > d_frac * total).astype(np.uint8)  # Dirichlet first along the outer arc
+        V = np.concatenate([outer, hole])
+        P = np.concatenate([closed_polyline(outer), closed_polyline(hole) + n_out])
+        flags = np.concatenate([oflags, np.ones(n_hole, np.uint8)])
+        sc = _make(2, V, P, flags, "sin2x_cos3y", (), True, "analytic")
+        sc["points"] = sample_inside_2d(rng, n_points, outer, holes=(hole,))
+    else:
+        m = 8
+        n_t = max(200, n_prims - 6 * 2 * m * m)
+        nv = max(8, int(np.sqrt(n_t / 2 / 2.5)))
+        nu = max(8, int(n_t / 2 / nv))
+        Vc, Pc = cube_mesh(m)
+        Vt, Pt, tube_radius = torus_mesh(nu, nv, seed=seed)
+        cz = Vt[Pt].mean(1)[:, 2]
+        # Dirichlet: the cube plus the torus below a z threshold
+        want_d = d_frac * (len(Pc) + len(Pt)) - len(Pc)
+        zt = np.quantile(cz, np.clip(want_d / len(Pt), 0, 1)) if want_d > 0 else -np.inf
+        tflags = (cz >= zt).astype(np.uint8)
+        V = np.concatenate([Vc, Vt])
+        P = np.concatenate([Pc, Pt + len(Vc)])
+        flags = np.concatenate([np.zeros(len(Pc), np.uint8), tflags])
+        sc = _make(3, V, P, flags, "quad3", (), False, "per_corner")
+        pts = []
+        while sum(len(p) for p in pts) < n_points:
+            q = rng.uniform(-0.95, 0.95, (4 * n_points + 16, 3))
+            rho, rs = tube_radius(q)
+            pts.append(q[rho > rs + 2e-3])
+        sc["points"] = np.concatenate(pts)[:n_points].astype(np.float32)
+    sc["walks"] = int(walks)
+    sc["epsilon"] = 1e-3
+    sc["r_min"] = 1e-3
+    sc["max_steps"] = 16384
+    sc["seed"] = int(seed)
+    sc["name"] = f"batch{i}_{dim}d_{len(sc['prims'])}p"
+    return sc
+
+
+def config4(n_scenes=64, seed=4001, prims=(1e3, 5e5), points=(1, 1e6), walks=(16, 4096), max_scene=None):
+    """The batched workload: n_scenes scenes, dimension by coin flip,
+    primitive counts, point counts and walks per point log-uniform over the
+    given ranges, Dirichlet fraction U(0.2, 0.8).  Returns scene dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        dim = 2 if rng.random() < 0.5 else 3
+        n_p = int(np.exp(rng.uniform(np.log(prims[0]), np.log(prims[1]))))
+        n_x = int(np.exp(rng.uniform(np.log(points[0]), np.log(points[1]))))
+        w = int(np.exp(rng.uniform(np.log(walks[0]), np.log(walks[1]))))
+        f = rng.uniform(0.2, 0.8)
+        if max_scene:
+            n_p = min(n_p, max_scene)
+        out.append(batched_scene(i, n_p, dim, f, max(1, n_x), max(1, w), seed * 100 + i))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Workload 5: resident 3D scenes and a Poisson stream of requests
+# ---------------------------------------------------------------------------
+def config5_scenes(n_scenes=8, total=5_000_000, lo=2e4, hi=2e6, seed=5001):
+    """Resident 3D scenes (cube + noisy torus like workload 3) whose torus
+    triangle counts are log-uniform in [lo, hi], rescaled to sum to about
+    `total`."""
+    rng = np.random.default_rng(seed)
+    t = np.exp(rng.uniform(np.log(lo), np.log(hi), n_scenes))
+    t = t * total / t.sum()
+    out = []
+    for i, n_t in enumerate(t):
+        nv = max(8, int(np.sqrt(n_t / 2 / 2.5)))
+        nu = max(8, int(n_t / 2 / nv))
+        sc = config3(grid=4, nu=nu, nv=nv, seed=seed * 10 + i)
+        sc["tube"] = (0.5, 0.2, 0.03, seed * 10 + i)
+        sc["name"] = f"serve{i}_torus{nu}x{nv}"
+        out.append(sc)
+    return out
+
+
+def plane_points(rng, n, tube):
+    """n points uniform on a random plane slice of [-1,1]^3 (unit normal,
+    offset U(-0.8, 0.8)), outside the torus of `tube` = (R, r, amp, seed)."""
+    R, r, amp, tseed = tube
+    nrm = rng.normal(size=3)
+    nrm /= np.linalg.norm(nrm)
+    off = rng.uniform(-0.8, 0.8)
+    a = np.cross(nrm, [1.0, 0, 0] if abs(nrm[0]) < 0.9 else [0, 1.0, 0])
+    a /= np.linalg.norm(a)
+    b = np.cross(nrm, a)
+    out = []
+    got = 0
+    while got < n:
+        uv = rng.uniform(-1.8, 1.8, (4 * n + 64, 2))
+        q = off * nrm + uv[:, :1] * a + uv[:, 1:] * b
+        q = q[np.all(np.abs(q) < 0.97, axis=1)]
+        tq = np.arctan2(q[:, 1], q[:, 0])
+        ring = np.stack([R * np.cos(tq), R * np.sin(tq), np.zeros(len(q))], 1)
+        dq = q - ring
+        rho = np.linalg.norm(dq, axis=1)
+        bq = ring + r * dq / np.maximum(rho, 1e-12)[:, None]
+        rs = r + amp * value_noise(bq, tseed)
+        q = q[rho > rs + 2e-3]
+        out.append(q)
+        got += len(q)
+    return np.concatenate(out)[:n].astype(np.float32)
+
+
+def config5_requests(duration_s=600.0, rate=200.0, n_scenes=8, seed=5002, points=(1e3, 2.56e5)):
+    """Poisson arrivals: (time, scene id, n_points, target SE, seed)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration_s:
+            break
+        n = int(np.exp(rng.uniform(np.log(points[0]), np.log(points[1]))))
+        out.append({"t": t, "scene": int(rng.integers(n_scenes)), "n_points": n,
+                    "target_se": 1e-2 if rng.random() < 0.5 else 1e-3, "seed": int(rng.integers(1 << 62))})
+    return out

@@ -81,6 +81,11 @@ _SIGS = {
     "wost_solve_destroy": [C.c_void_p],
     "wost_solve_device_accumulators": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "wost_solve_work_counts": [C.c_void_p, C.c_void_p],
+    "wost_solve_batch": [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "wost_engine_create": [C.c_void_p, C.POINTER(C.c_void_p)],
+    "wost_engine_submit": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_void_p)],
+    "wost_engine_get_stats": [C.c_void_p, C.c_void_p],
+    "wost_engine_destroy": [C.c_void_p],
     "wost_query_closest_dirichlet": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p],
     "wost_query_silhouette": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -217,8 +222,77 @@ def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=102
     """Starts a solve.  `points` is a numpy array (host) or a torch CUDA
     tensor (device); normals/on_neumann likewise.  Returns the handle."""
     lib = load()
-    d = wost_solve_desc()
     keep = []
+    d = _solve_desc(keep, points, walks_per_point, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
+                    normals, on_neumann, stream)
+    h = C.c_void_p()
+    _check(lib.wost_solve(scene, C.byref(d), C.byref(h)))
+    return h
+
+
+def wost_solve_batch(scenes, requests, stream=None):
+    """One batched persistent launch (per dimension) for many solves.
+    `requests` is a list of dicts with the keyword arguments of wost_solve.
+    Returns one handle per request."""
+    lib = load()
+    n = len(requests)
+    keep = []
+    arr = (wost_solve_desc * n)()
+    for i, rq in enumerate(requests):
+        rq = dict(rq)
+        pts = rq.pop("points")
+        arr[i] = _solve_desc(keep, pts, **rq)
+    sc = (C.c_void_p * n)(*[s.value if isinstance(s, C.c_void_p) else s for s in scenes])
+    out = (C.c_void_p * n)()
+    _check(lib.wost_solve_batch(n, sc, arr, _stream_ptr(stream), out))
+    return [C.c_void_p(h) for h in out]
+
+
+class wost_engine_desc(C.Structure):
+    _fields_ = [("device", C.c_int32), ("memory_budget_bytes", C.c_int64), ("round_seconds", C.c_double),
+                ("min_walks", C.c_int32), ("max_walks_per_point", C.c_int32), ("block_size", C.c_int32)]
+
+
+class wost_engine_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("rejected", C.c_uint64), ("capped", C.c_uint64), ("queued", C.c_int32),
+                ("active", C.c_int32), ("rounds", C.c_uint64), ("gpu_seconds", C.c_double),
+                ("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("round_budget_steps", C.c_double)]
+
+
+def wost_engine_create(device=0, memory_budget_bytes=0, round_seconds=0.0, min_walks=0, max_walks_per_point=0,
+                       block_size=0):
+    lib = load()
+    d = wost_engine_desc(device, memory_budget_bytes, round_seconds, min_walks, max_walks_per_point, block_size)
+    h = C.c_void_p()
+    _check(lib.wost_engine_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def wost_engine_submit(engine, scene, points, target_se, walks_cap=0, epsilon=1e-3, r_min=0.0, max_steps=1024,
+                       seed=0, first_walk=0, normals=None, on_neumann=None):
+    lib = load()
+    keep = []
+    d = _solve_desc(keep, points, walks_cap, epsilon, r_min, max_steps, seed, first_walk, "persistent", 0, normals,
+                    on_neumann, None)
+    h = C.c_void_p()
+    _check(lib.wost_engine_submit(engine, scene, C.byref(d), float(target_se), C.byref(h)))
+    return h
+
+
+def wost_engine_get_stats(engine) -> dict:
+    s = wost_engine_stats()
+    _check(load().wost_engine_get_stats(engine, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in wost_engine_stats._fields_}
+
+
+def wost_engine_destroy(engine):
+    _check(load().wost_engine_destroy(engine))
+
+
+def _solve_desc(keep, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
+                kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None):
+    d = wost_solve_desc()
     if isinstance(points, np.ndarray):
         pts = np.ascontiguousarray(points, np.float32)
         keep.append(pts)
@@ -248,9 +322,7 @@ def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=102
     d.kernel = KERNEL[kernel] if isinstance(kernel, str) else int(kernel)
     d.block_size = int(block_size)
     d.stream = _stream_ptr(stream)
-    h = C.c_void_p()
-    _check(lib.wost_solve(scene, C.byref(d), C.byref(h)))
-    return h
+    return d
 
 
 def wost_poll(solve, n_points):
