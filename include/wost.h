@@ -249,6 +249,7 @@ typedef struct {
     uint64_t submitted, admitted, completed, cancelled, rejected, capped;
     int32_t queued, active;
     uint64_t rounds;
+    uint64_t graph_launches;      /* rounds launched by replaying a CUDA graph   */
     double gpu_seconds;           /* summed GPU time of finished rounds          */
     int64_t budget_bytes, used_bytes;
     double round_budget_steps;    /* current walk-step budget of one round       */
@@ -302,6 +303,24 @@ wost_status wost_query_intersect_neumann(wost_scene *scene, int64_t n, const flo
 wost_status wost_query_neumann_sample(wost_scene *scene, int64_t n, const float *points,
                                       const float *r, uint64_t seed, uint32_t ctr1, uint32_t ctr2,
                                       float *z, float *pdf, int32_t *prim, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuning                                                              */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t block_size;         /* fastest threads per block                     */
+    double steps_per_second;    /* its walk-step rate on the sample              */
+    int32_t n_tried;
+    int32_t tried_block[8];
+    double tried_steps_per_second[8];
+} wost_tune_result;
+
+/* Times the persistent kernel on a sample of the caller's points (device
+ * pointer, n points, at most 8192 used) for block sizes 64..256 and keeps
+ * the fastest as the scene's default for persistent, batched and engine
+ * launches whose block_size is 0.  Same validation as wost_solve. */
+wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t n, int32_t walks_per_point,
+                                float epsilon, float r_min, int32_t max_steps, wost_tune_result *out);
 
 /* Thread-local description of the last failure on this thread. */
 const char *wost_last_error(void);

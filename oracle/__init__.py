@@ -92,7 +92,7 @@ def _L():
             lib.orc_source_radius.restype = C.c_double
             lib.orc_source_radius.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
             lib.orc_solve.restype = C.c_int
-            lib.orc_solve.argtypes = [P, C.c_int64, P, P, P, C.c_int, C.c_uint32, P, P, P, P, P, P]
+            lib.orc_solve.argtypes = [P, C.c_int64, P, P, P, C.c_int, C.c_uint32, C.c_uint32, P, P, P, P, P, P]
             lib.orc_walk_trace.restype = C.c_int
             lib.orc_walk_trace.argtypes = [P, P, P, C.c_int, C.c_uint32, C.c_uint32, P, P,
                                            C.c_int, P, P]
@@ -230,8 +230,9 @@ def _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads):
 
 def solve(scene: Scene, points, walks: int, epsilon: float, r_min=None, max_steps=1024, seed=0,
           normals=None, on_neumann=None, first_walk=0, offset=DEFAULT_OFFSET,
-          vis_tmax=DEFAULT_VIS_TMAX, threads=0, per_walk=False) -> dict:
-    """Runs `walks` walks from every point; returns per-point FP64 statistics."""
+          vis_tmax=DEFAULT_VIS_TMAX, threads=0, per_walk=False, point_base=0) -> dict:
+    """Runs `walks` walks from every point; returns per-point FP64 statistics.
+    Point i uses the random stream of point index point_base + i."""
     x = _d(points)
     n = len(x)
     nr = None if normals is None else _d(normals)
@@ -241,7 +242,7 @@ def solve(scene: Scene, points, walks: int, epsilon: float, r_min=None, max_step
     pw = np.zeros(n * walks) if per_walk else None
     p = _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads)
     used = _L().orc_solve(scene._h, n, _ptr(x), _ptr(nr), _ptr(on), int(walks), int(first_walk),
-                          C.byref(p), _ptr(sm), _ptr(sq), _ptr(st), _ptr(cp), _ptr(pw))
+                          int(point_base), C.byref(p), _ptr(sm), _ptr(sq), _ptr(st), _ptr(cp), _ptr(pw))
     mean = sm / walks
     var = np.maximum(sq / walks - mean**2, 0.0) * walks / max(walks - 1, 1)
     out = dict(mean=mean, se=np.sqrt(var / walks), sum=sm, sumsq=sq, steps=st, capped=cp,

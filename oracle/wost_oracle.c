@@ -915,6 +915,7 @@ typedef struct {
     const uint8_t *onN;
     int walks;
     uint32_t first_walk;
+    uint32_t point_base;
     const orc_params *p;
     double *sum, *sumsq, *per_walk;
     int64_t *steps, *capped;
@@ -937,7 +938,7 @@ static void *worker(void *arg) {
         int64_t st = 0, cp = 0;
         for (int j = 0; j < J->walks; ++j) {
             int steps, capped;
-            double val = walk(J->s, x0, n0, on, (uint32_t)i, J->first_walk + (uint32_t)j, J->p, &steps,
+            double val = walk(J->s, x0, n0, on, J->point_base + (uint32_t)i, J->first_walk + (uint32_t)j, J->p, &steps,
                               &capped, NULL, 0, NULL);
             sm += val;
             sq += val * val;
@@ -955,9 +956,10 @@ static void *worker(void *arg) {
 
 int orc_solve(const orc_scene *s, int64_t n, const double *points, const double *normals,
               const uint8_t *on_neumann, int walks_per_point, uint32_t first_walk,
-              const orc_params *p, double *out_sum, double *out_sumsq, int64_t *out_steps,
-              int64_t *out_capped, double *per_walk) {
+              uint32_t point_base, const orc_params *p, double *out_sum, double *out_sumsq,
+              int64_t *out_steps, int64_t *out_capped, double *per_walk) {
     job_t J;
+    J.point_base = point_base;
     J.s = s; J.n = n; J.points = points; J.normals = normals; J.onN = on_neumann;
     J.walks = walks_per_point; J.first_walk = first_walk; J.p = p;
     J.sum = out_sum; J.sumsq = out_sumsq; J.steps = out_steps; J.capped = out_capped;

@@ -114,13 +114,14 @@ typedef struct {
 } orc_params;
 
 /* Runs walks_per_point walks (walk ids first_walk ...) from each point and
- * writes FP64 per-point sums.  normals/on_neumann may be NULL.  per_walk,
- * if not NULL, receives every walk's estimate [n * walks]. */
+ * writes FP64 per-point sums.  Point i draws the random stream of point
+ * index point_base + i.  normals/on_neumann may be NULL.  per_walk, if not
+ * NULL, receives every walk's estimate [n * walks]. */
 int orc_solve(const orc_scene *s, int64_t n, const double *points,
               const double *normals, const uint8_t *on_neumann,
-              int walks_per_point, uint32_t first_walk, const orc_params *p,
-              double *out_sum, double *out_sumsq, int64_t *out_steps,
-              int64_t *out_capped, double *per_walk);
+              int walks_per_point, uint32_t first_walk, uint32_t point_base,
+              const orc_params *p, double *out_sum, double *out_sumsq,
+              int64_t *out_steps, int64_t *out_capped, double *per_walk);
 
 /* One walk with a per-step trace.  Each row has ORC_TRACE_COLS doubles:
  * x0 x1 x2 onNeumann d_D d_sil r hit t_boundary N S.  Returns the number of

@@ -76,6 +76,7 @@ struct wost_scene {
     wost::SceneView *view_dev = nullptr;  // device copy of `view` (batched launches)
     wost_scene_info info{};
     int stack_depth = 0;
+    int tuned_block = 0;                  // set by wost_scene_autotune (0 = not tuned)
     std::mutex mu;
     ~wost_scene() {
         if (guard) cudaFree(guard);

@@ -156,7 +156,7 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
         return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
     if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING)
         return fail(WOST_ERR_INVALID_ARG, "unknown kernel");
-    int block = d->block_size ? d->block_size : 128;
+    int block = d->block_size ? d->block_size : (scene->tuned_block ? scene->tuned_block : 128);
     if (block < 32 || block > 256 || block % 32)
         return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
     CK(cudaSetDevice(scene->device), "cudaSetDevice");
@@ -301,7 +301,8 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
             stream = shared->own_stream;
         }
         std::vector<std::unique_ptr<wost_solve_handle>> hs(n);
-        int block = descs[0].block_size ? descs[0].block_size : 128;
+        int block = descs[0].block_size ? descs[0].block_size
+                                        : (scenes[0]->tuned_block ? scenes[0]->tuned_block : 128);
         for (int32_t i = 0; i < n; ++i) {
             hs[i].reset(new wost_solve_handle);
             wost_solve_desc d = descs[i];
@@ -326,12 +327,18 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
             depth[di] = std::max(depth[di], scenes[i]->stack_depth);
             jobs[di].push_back(j);
         }
+        // device layout per dimension: BatchHeader, then the jobs
+        std::vector<unsigned char> staging[2];
         for (int di = 0; di < 2; ++di) {
             for (auto &j : jobs[di]) j.sp.stack_depth = depth[di];
-            CK(shared->jobs[di].alloc(jobs[di].size() * sizeof(BatchJob)), "cudaMalloc jobs");
+            BatchHeader hd{(int)jobs[di].size(), 0, shared->total[di]};
+            staging[di].resize(sizeof(BatchHeader) + jobs[di].size() * sizeof(BatchJob));
+            std::memcpy(staging[di].data(), &hd, sizeof hd);
             if (!jobs[di].empty())
-                CK(cudaMemcpyAsync(shared->jobs[di].p, jobs[di].data(), jobs[di].size() * sizeof(BatchJob),
-                                   cudaMemcpyHostToDevice, stream), "copy jobs");
+                std::memcpy(staging[di].data() + sizeof hd, jobs[di].data(), jobs[di].size() * sizeof(BatchJob));
+            CK(shared->jobs[di].alloc(staging[di].size()), "cudaMalloc jobs");
+            CK(cudaMemcpyAsync(shared->jobs[di].p, staging[di].data(), staging[di].size(), cudaMemcpyHostToDevice,
+                               stream), "copy jobs");
         }
         CK(shared->counters.alloc(4 * 8), "cudaMalloc counters");
         CK(cudaMemsetAsync(shared->counters.p, 0, 4 * 8, stream), "memset");
@@ -346,7 +353,8 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
             if (jobs[di].empty()) continue;
             int blocks = 0;
             CK(batch_grid(di + 2, block, depth[di], &blocks), "occupancy");
-            CK(launch_walk_batch(di + 2, (const BatchJob *)shared->jobs[di].p, (int)jobs[di].size(), shared->total[di],
+            const unsigned char *base = (const unsigned char *)shared->jobs[di].p;
+            CK(launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)),
                                  ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, stream),
                "kernel launch");
         }
@@ -569,6 +577,54 @@ wost_status wost_query_neumann_sample(wost_scene *s, int64_t n, const float *pts
     cudaError_t e = launch_query_sample(s->view, n, pts, r, (uint32_t)seed, (uint32_t)(seed >> 32), ctr1, ctr2, z, pdf,
                                         prim, (cudaStream_t)stream);
     return query_epilogue(s, e, (cudaStream_t)stream);
+}
+
+wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t n, int32_t walks, float epsilon,
+                                float r_min, int32_t max_steps, wost_tune_result *out) {
+    try {
+        if (!scene || !points || !out || n < 1) return fail(WOST_ERR_INVALID_ARG, "null argument or n < 1");
+        std::memset(out, 0, sizeof *out);
+        const int64_t m = std::min<int64_t>(n, 8192);
+        const int blocks[4] = {64, 128, 192, 256};
+        double best = -1;
+        for (int bi = 0; bi < 4; ++bi) {
+            wost_solve_desc d{};
+            d.n_points = m;
+            d.points = points;
+            d.memory = WOST_MEM_DEVICE;
+            d.walks_per_point = walks > 0 ? walks : 32;
+            d.epsilon = epsilon;
+            d.r_min = r_min;
+            d.max_steps = max_steps;
+            d.seed = 0x5EED0000u + (uint64_t)bi;
+            d.kernel = WOST_KERNEL_PERSISTENT;
+            d.block_size = blocks[bi];
+            double rate = 0;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and the module
+                wost_solve_handle *h = nullptr;
+                wost_status st = wost_solve(scene, &d, &h);
+                if (st != WOST_OK) return st;
+                st = wost_wait(h, -1);
+                wost_progress pr{};
+                if (st == WOST_OK) st = wost_poll(h, nullptr, nullptr, nullptr, &pr);
+                wost_solve_destroy(h);
+                if (st != WOST_OK) return st;
+                rate = pr.elapsed_seconds > 0 ? (double)pr.total_steps / pr.elapsed_seconds : 0;
+            }
+            out->tried_block[out->n_tried] = blocks[bi];
+            out->tried_steps_per_second[out->n_tried] = rate;
+            out->n_tried++;
+            if (rate > best) {
+                best = rate;
+                out->block_size = blocks[bi];
+                out->steps_per_second = rate;
+            }
+        }
+        scene->tuned_block = out->block_size;
+        return WOST_OK;
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
 }
 
 }  // extern "C"

@@ -50,15 +50,31 @@ struct Piece {
     int w0, nw;
 };
 
+// One scheduling slot: device job tables (BatchHeader + jobs, per
+// dimension), their pinned staging copies, and the CUDA graph of one round:
+// reset counters, upload both tables, launch the 2D and the 3D batched
+// kernels (a kernel whose table is empty returns at once).  A round replays
+// the graph; it is re-captured only when a table outgrows its capacity or a
+// deeper scene needs a larger traversal stack.
 struct Slot {
     DevBuf jobs[2];
-    size_t cap[2] = {0, 0};
-    BatchJob *host = nullptr;  // pinned staging
-    size_t host_cap = 0;
+    unsigned char *host[2] = {nullptr, nullptr};
+    size_t cap[2] = {0, 0};    // jobs per table
+    int depth[2] = {0, 0};     // stack entries the graph was captured with
     DevBuf counters;           // next walk 2D, next walk 3D, guard
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool busy = false;
+    ~Slot() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto *h : host)
+            if (h) cudaFreeHost(h);
+    }
 };
+
+size_t table_bytes(size_t jobs) { return sizeof(BatchHeader) + jobs * sizeof(BatchJob); }
 
 struct Round {
     int slot;
@@ -243,6 +259,57 @@ void process_cancels(wost_engine *e) {
     for (Request *r : done) finish(e, r, WOST_ERR_CANCELLED);
 }
 
+// (Re)captures the slot's round graph if its tables are too small for this
+// round or a scene needs a deeper stack than the graph was captured with.
+cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const int depth[2]) {
+    bool rebuild = sl.exec == nullptr;
+    cudaError_t er;
+    for (int di = 0; di < 2; ++di) {
+        if (cnt[di] > sl.cap[di] || !sl.host[di]) {
+            size_t nc = std::max<size_t>(std::max<size_t>(cnt[di], 2 * sl.cap[di]), 16);
+            if (sl.host[di]) cudaFreeHost(sl.host[di]);
+            sl.host[di] = nullptr;
+            if ((er = cudaMallocHost((void **)&sl.host[di], table_bytes(nc))) != cudaSuccess) return er;
+            std::memset(sl.host[di], 0, sizeof(BatchHeader));
+            sl.jobs[di].~DevBuf();
+            new (&sl.jobs[di]) DevBuf();
+            if ((er = sl.jobs[di].alloc(table_bytes(nc))) != cudaSuccess) return er;
+            sl.cap[di] = nc;
+            rebuild = true;
+        }
+        int want = std::max(depth[di], 2);
+        if (want > sl.depth[di]) {
+            sl.depth[di] = want;
+            rebuild = true;
+        }
+    }
+    if (!sl.counters.p) {
+        if ((er = sl.counters.alloc(3 * 8)) != cudaSuccess) return er;
+        rebuild = true;
+    }
+    if (!rebuild) return cudaSuccess;
+    if (sl.exec) cudaGraphExecDestroy(sl.exec);
+    if (sl.graph) cudaGraphDestroy(sl.graph);
+    sl.exec = nullptr;
+    sl.graph = nullptr;
+    int blocks[2];
+    for (int di = 0; di < 2; ++di)
+        if ((er = batch_grid(di + 2, e->block, sl.depth[di], &blocks[di])) != cudaSuccess) return er;
+    unsigned long long *ctr = (unsigned long long *)sl.counters.p;
+    if ((er = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return er;
+    cudaMemsetAsync(sl.counters.p, 0, 3 * 8, e->stream);
+    for (int di = 0; di < 2; ++di)
+        cudaMemcpyAsync(sl.jobs[di].p, sl.host[di], table_bytes(sl.cap[di]), cudaMemcpyHostToDevice, e->stream);
+    for (int di = 0; di < 2; ++di) {
+        const unsigned char *base = (const unsigned char *)sl.jobs[di].p;
+        launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)), ctr + di,
+                          (unsigned int *)(ctr + 2), sl.depth[di], nullptr, e->block, blocks[di], e->stream);
+    }
+    er = cudaStreamEndCapture(e->stream, &sl.graph);
+    if (er != cudaSuccess) return er;
+    return cudaGraphInstantiate(&sl.exec, sl.graph, 0);
+}
+
 bool launch_round(wost_engine *e) {
     int si = -1;
     for (int i = 0; i < 3; ++i)
@@ -276,19 +343,8 @@ bool launch_round(wost_engine *e) {
             remaining -= (double)np * cost;
         }
     }
-    // job tables per dimension
+    // job tables per dimension, written into the slot's pinned staging
     Slot &sl = e->slots[si];
-    size_t np = rd.pieces.size();
-    if (np > sl.host_cap) {
-        if (sl.host) cudaFreeHost(sl.host);
-        sl.host_cap = std::max<size_t>(np, 2 * sl.host_cap);
-        if (cudaMallocHost((void **)&sl.host, sl.host_cap * sizeof(BatchJob)) != cudaSuccess) {
-            sl.host = nullptr;
-            sl.host_cap = 0;
-            for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_OUT_OF_MEMORY);
-            return false;
-        }
-    }
     size_t cnt[2] = {0, 0};
     int depth[2] = {0, 0};
     for (auto &p : rd.pieces) {
@@ -296,9 +352,15 @@ bool launch_round(wost_engine *e) {
         cnt[di]++;
         depth[di] = std::max(depth[di], p.r->scene->stack_depth);
     }
-    size_t off[2] = {0, cnt[0]};
+    cudaError_t err = ensure_graph(e, sl, cnt, depth);
+    if (err != cudaSuccess) {
+        for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_CUDA);
+        return false;
+    }
     unsigned long long total[2] = {0, 0};
     size_t fill[2] = {0, 0};
+    BatchJob *tab[2] = {(BatchJob *)(sl.host[0] + sizeof(BatchHeader)),
+                        (BatchJob *)(sl.host[1] + sizeof(BatchHeader))};
     for (auto &p : rd.pieces) {
         int di = p.r->h->dim - 2;
         BatchJob j;
@@ -308,40 +370,25 @@ bool launch_round(wost_engine *e) {
         j.sp.n_points = p.np;
         j.sp.walks_per_point = p.nw;
         j.sp.first_walk = p.r->h->sp.first_walk + (uint32_t)p.w0;
-        j.sp.stack_depth = depth[di];
+        j.sp.stack_depth = sl.depth[di];
         j.acc = p.r->h->acc;
         j.walk_begin = total[di];
         total[di] += (unsigned long long)p.np * (unsigned long long)p.nw;
-        sl.host[off[di] + fill[di]++] = j;
+        tab[di][fill[di]++] = j;
     }
-    if (!sl.counters.p) sl.counters.alloc(3 * 8);
-    cudaMemsetAsync(sl.counters.p, 0, 3 * 8, e->stream);
+    for (int di = 0; di < 2; ++di) {
+        BatchHeader hd{(int)cnt[di], 0, total[di]};
+        std::memcpy(sl.host[di], &hd, sizeof hd);
+    }
     cudaEventRecord(sl.ev0, e->stream);
-    unsigned long long *ctr = (unsigned long long *)sl.counters.p;
-    cudaError_t err = cudaSuccess;
-    for (int di = 0; di < 2 && err == cudaSuccess; ++di) {
-        if (!cnt[di]) continue;
-        if (cnt[di] > sl.cap[di]) {
-            sl.jobs[di].~DevBuf();
-            new (&sl.jobs[di]) DevBuf();
-            sl.cap[di] = std::max<size_t>(cnt[di], 2 * sl.cap[di]);
-            err = sl.jobs[di].alloc(sl.cap[di] * sizeof(BatchJob));
-            if (err != cudaSuccess) break;
-        }
-        err = cudaMemcpyAsync(sl.jobs[di].p, sl.host + off[di], cnt[di] * sizeof(BatchJob), cudaMemcpyHostToDevice,
-                              e->stream);
-        int blocks = 0;
-        if (err == cudaSuccess) err = batch_grid(di + 2, e->block, depth[di], &blocks);
-        if (err == cudaSuccess)
-            err = launch_walk_batch(di + 2, (const BatchJob *)sl.jobs[di].p, (int)cnt[di], total[di], ctr + di,
-                                    (unsigned int *)(ctr + 2), depth[di], nullptr, e->block, blocks, e->stream);
-    }
+    err = cudaGraphLaunch(sl.exec, e->stream);
     cudaEventRecord(sl.ev1, e->stream);
     if (err != cudaSuccess) {
         for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_CUDA);
         cudaStreamSynchronize(e->stream);
         return false;
     }
+    e->st.graph_launches++;
     sl.busy = true;
     e->inflight.push_back(std::move(rd));
     return true;
@@ -546,7 +593,6 @@ wost_status wost_engine_destroy(wost_engine *e) {
     }
     e->by_handle.clear();
     for (auto &s : e->slots) {
-        if (s.host) cudaFreeHost(s.host);
         if (s.ev0) cudaEventDestroy(s.ev0);
         if (s.ev1) cudaEventDestroy(s.ev1);
     }

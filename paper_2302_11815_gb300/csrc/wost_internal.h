@@ -103,6 +103,14 @@ struct StatJob {
     int64_t n;
 };
 
+// Size of a batched launch, read by the kernel from device memory so that a
+// captured graph can be replayed with new job tables.
+struct BatchHeader {
+    int n_jobs;
+    int pad;
+    unsigned long long total;  // walks in the launch
+};
+
 // One entry of a batched launch: a solve's walks [walk_begin, walk_begin +
 // n_points * walks_per_point) in the launch's walk index space.
 struct BatchJob {

@@ -126,9 +126,12 @@ __global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, con
 // the jobs' walks; a lane maps its next index to a job by binary search over
 // the jobs' first indices and runs that job's walk on that job's scene.
 template <int D>
-__global__ void __launch_bounds__(256) k_walk_batch(const BatchJob *__restrict__ jobs, int n_jobs,
-                                                    unsigned long long total, unsigned long long *counter,
+__global__ void __launch_bounds__(256) k_walk_batch(const BatchHeader *__restrict__ hdr,
+                                                    const BatchJob *__restrict__ jobs, unsigned long long *counter,
                                                     unsigned int *guard, int stack_depth, const int *cancel) {
+    const int n_jobs = hdr->n_jobs;
+    const unsigned long long total = hdr->total;
+    if (n_jobs <= 0) return;
     Stack st = make_stack(stack_depth, guard);
     const int lane = threadIdx.x & 31;
     Walk w;
@@ -373,14 +376,14 @@ cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
     return cudaSuccess;
 }
 
-cudaError_t launch_walk_batch(int dim, const BatchJob *jobs, int n_jobs, unsigned long long total,
-                              unsigned long long *counter, unsigned int *guard, int depth, const int *cancel,
-                              int block, int blocks, cudaStream_t s) {
+cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
+                              unsigned int *guard, int depth, const int *cancel, int block, int blocks,
+                              cudaStream_t s) {
     size_t sm = smem_bytes(depth, block);
     if (dim == 2)
-        k_walk_batch<2><<<blocks, block, sm, s>>>(jobs, n_jobs, total, counter, guard, depth, cancel);
+        k_walk_batch<2><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
     else
-        k_walk_batch<3><<<blocks, block, sm, s>>>(jobs, n_jobs, total, counter, guard, depth, cancel);
+        k_walk_batch<3><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
     return cudaGetLastError();
 }
 

@@ -16,9 +16,9 @@ cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out);
 cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_points, unsigned int *max_var_bits,
                                  unsigned long long *min_walks, unsigned long long *steps_sum,
                                  unsigned long long *walks_sum, cudaStream_t s);
-cudaError_t launch_walk_batch(int dim, const BatchJob *jobs, int n_jobs, unsigned long long total,
-                              unsigned long long *counter, unsigned int *guard, int depth, const int *cancel,
-                              int block, int blocks, cudaStream_t s);
+cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
+                              unsigned int *guard, int depth, const int *cancel, int block, int blocks,
+                              cudaStream_t s);
 cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
                                    int blocks, cudaStream_t s);
 cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pts, float *dist, float *closest,

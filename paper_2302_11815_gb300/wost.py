@@ -86,6 +86,8 @@ _SIGS = {
     "wost_engine_submit": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(C.c_void_p)],
     "wost_engine_get_stats": [C.c_void_p, C.c_void_p],
     "wost_engine_destroy": [C.c_void_p],
+    "wost_scene_autotune": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_int32,
+                            C.c_void_p],
     "wost_query_closest_dirichlet": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p],
     "wost_query_silhouette": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -256,7 +258,8 @@ class wost_engine_desc(C.Structure):
 class wost_engine_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("cancelled", C.c_uint64), ("rejected", C.c_uint64), ("capped", C.c_uint64), ("queued", C.c_int32),
-                ("active", C.c_int32), ("rounds", C.c_uint64), ("gpu_seconds", C.c_double),
+                ("active", C.c_int32), ("rounds", C.c_uint64), ("graph_launches", C.c_uint64),
+                ("gpu_seconds", C.c_double),
                 ("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("round_budget_steps", C.c_double)]
 
 
@@ -278,6 +281,21 @@ def wost_engine_submit(engine, scene, points, target_se, walks_cap=0, epsilon=1e
     h = C.c_void_p()
     _check(lib.wost_engine_submit(engine, scene, C.byref(d), float(target_se), C.byref(h)))
     return h
+
+
+class wost_tune_result(C.Structure):
+    _fields_ = [("block_size", C.c_int32), ("steps_per_second", C.c_double), ("n_tried", C.c_int32),
+                ("tried_block", C.c_int32 * 8), ("tried_steps_per_second", C.c_double * 8)]
+
+
+def wost_scene_autotune(scene, points, walks_per_point=32, epsilon=1e-3, r_min=0.0, max_steps=1024) -> dict:
+    """Times block sizes on a sample of the (device) points; the fastest
+    becomes the scene's default."""
+    r = wost_tune_result()
+    _check(load().wost_scene_autotune(scene, _dptr(points), points.shape[0], int(walks_per_point), float(epsilon),
+                                      float(r_min), int(max_steps), C.byref(r)))
+    return {"block_size": r.block_size, "steps_per_second": r.steps_per_second,
+            "tried": {int(r.tried_block[i]): float(r.tried_steps_per_second[i]) for i in range(r.n_tried)}}
 
 
 def wost_engine_get_stats(engine) -> dict:
