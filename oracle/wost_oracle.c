@@ -45,6 +45,7 @@
  *      One fresh uniform per reservoir candidate in the leaf.
  *   R7 2D source radius t = R sqrt(U1 U2); 3D t = R (1/2 + sin(asin(2U-1)/3))
  *      (inverse CDF of Beta(2,2)); both are the normalised G_B of App. A.
+ *   R12 a Neumann sample at distance exactly 0 from x contributes nothing.
  */
 #include "wost_oracle.h"
 
@@ -860,7 +861,9 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
         double Nterm = 0.0;
         if (zprim >= 0 && pdf > 0) {
             double dz = len(sub(z, x));
-            if (dz < r) {
+            /* R12: a sample at zero distance from x (G infinite, a set of
+             * measure zero reached only through rounding) is skipped */
+            if (dz < r && dz > 0) {
                 double tvis;
                 int vp;
                 int occluded = q_intersect_neumann(s, xq, sub(z, xq), pr->vis_tmax, zprim, &tvis, &vp);

@@ -17,7 +17,8 @@
 //   R5 at the step cap the walk ends with g at the closest Dirichlet point;
 //   R6 Q.4 child weight 1/d to the child box centre (the 1/(4 pi) of the
 //      free-space Green's function cancels in the child probabilities);
-//   R7 2D source radius R sqrt(U1 U2), 3D R (1/2 + sin(asin(2U-1)/3)).
+//   R7 2D source radius R sqrt(U1 U2), 3D R (1/2 + sin(asin(2U-1)/3));
+//   R12 a Neumann sample at distance 0 from x contributes nothing.
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11); key = seed, counter
 // = (walk, point, step, slot); slot 0 drives direction and source, slots
 // 1, 2, ... the Neumann sampler.
@@ -346,9 +347,12 @@ struct Closest {
 };
 
 template <int D, bool CN = false>
-__device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &cnt) {
+__device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &cnt, float bound2 = INFINITY) {
+    // bound2: a known upper bound on the squared distance (nodes farther away
+    // are pruned from the start); the caller retries without it if nothing
+    // lies within the bound
     Closest best;
-    best.d2 = INFINITY;
+    best.d2 = bound2;
     best.rec = -1;
     best.s0 = best.s1 = 0.f;
     best.p = x;
@@ -735,6 +739,7 @@ __device__ __forceinline__ float grid_eval(const FieldView &f, P3 y) {
 struct Walk {
     P3 x, n;
     float acc;
+    float dbound;  // upper bound on d_D at x: previous d_D + length of the move
     int steps;
     bool onN, capped;
     uint32_t point, index;
@@ -746,8 +751,12 @@ __device__ __forceinline__ float maxabs3(P3 a) { return fmaxf(fabsf(a.x), fmaxf(
 // estimate is then w.acc).
 template <int D, bool CN = false>
 __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, const Stack &st, Cnt<CN> &cnt) {
-    // distance to the Dirichlet boundary (Q.1)
-    Closest cl = q_closest<D, CN>(sc.D, w.x, st, cnt);
+    // distance to the Dirichlet boundary (Q.1).  The closest point of the
+    // previous step is at most dbound away (triangle inequality), which
+    // prunes the search; the result is the exact closest point either way.
+    float b = w.dbound * 1.0001f + 1e-6f;
+    Closest cl = q_closest<D, CN>(sc.D, w.x, st, cnt, b * b);
+    if (cl.rec < 0) cl = q_closest<D, CN>(sc.D, w.x, st, cnt);
     w.steps += 1;
     float dD = sqrtf(cl.d2);
     if (dD < sp.epsilon || w.steps >= sp.max_steps) {
@@ -802,7 +811,9 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
         if (zs.rec >= 0 && zs.pdf > 0.f) {
             P3 dz = zs.z - w.x;
             float dzl = sqrtf(dotp<D>(dz, dz));
-            if (dzl < r) {
+            // R12: a sample at zero distance (x and z rounded onto the same
+            // point of one primitive) has G = inf and measure zero: skipped
+            if (dzl < r && dzl > 0.f) {
                 float tv;
                 int occ = q_ray<D, true, CN>(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, tv, st, cnt);
                 if (occ < 0) {
@@ -839,6 +850,8 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     }
     // R1: the step adds the Neumann and source terms
     w.acc += Nterm + Sterm;
+    P3 mv = p - w.x;
+    w.dbound = dD + sqrtf(dotp<D>(mv, mv));
     w.x = p;
     w.n = np;
     w.onN = hrec >= 0;
@@ -860,6 +873,7 @@ __device__ __forceinline__ void walk_init(const SolveParams &sp, Walk &w, int64_
     w.onN = sp.on_neumann ? sp.on_neumann[point] != 0 : false;
     w.n = (w.onN && sp.normals) ? load_point<D>(sp.normals, point) : mk(0.f, 0.f, 0.f);
     w.acc = 0.f;
+    w.dbound = INFINITY;
     w.steps = 0;
     w.capped = false;
     w.point = (uint32_t)point;
