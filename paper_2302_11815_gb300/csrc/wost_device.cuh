@@ -357,13 +357,12 @@ __device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &
     best.s0 = best.s1 = 0.f;
     best.p = x;
     if (T.root == WOST_EMPTY_REF) return best;
+    // nearest-first depth-first search: the nearer child is visited next
+    // without a stack round trip, only the farther one is pushed
     int sp = 0;
-    spush(st, sp, T.root, box_dist2<D>(T.root_lo, T.root_hi, x));
-    while (sp > 0) {
-        uint32_t ref;
-        float key;
-        spop(st, sp, ref, key);
-        if (key >= best.d2) continue;
+    uint32_t ref = T.root;
+    if (box_dist2<D>(T.root_lo, T.root_hi, x) >= best.d2) return best;
+    for (;;) {
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -381,19 +380,29 @@ __device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &
                     best.p = q;
                 }
             }
-            continue;
-        }
-        cnt.node(C_Q1);
-        Node<D> n = load_node<D>(T.nodes, ref);
-        float d0 = box_dist2<D>(n.lo0, n.hi0, x), d1 = box_dist2<D>(n.lo1, n.hi1, x);
-        // push the farther child first so that the nearer one is popped next
-        if (d0 <= d1) {
-            if (d1 < best.d2) spush(st, sp, n.r1, d1);
-            if (d0 < best.d2) spush(st, sp, n.r0, d0);
         } else {
-            if (d0 < best.d2) spush(st, sp, n.r0, d0);
-            if (d1 < best.d2) spush(st, sp, n.r1, d1);
+            cnt.node(C_Q1);
+            Node<D> n = load_node<D>(T.nodes, ref);
+            float d0 = box_dist2<D>(n.lo0, n.hi0, x), d1 = box_dist2<D>(n.lo1, n.hi1, x);
+            bool h0 = d0 < best.d2, h1 = d1 < best.d2;
+            if (h0 && h1) {
+                bool first0 = d0 <= d1;
+                spush(st, sp, first0 ? n.r1 : n.r0, first0 ? d1 : d0);
+                ref = first0 ? n.r0 : n.r1;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? n.r0 : n.r1;
+                continue;
+            }
         }
+        // next pending subtree that can still hold something closer
+        float key = INFINITY;
+        while (sp > 0) {
+            spop(st, sp, ref, key);
+            if (key < best.d2) break;
+        }
+        if (!(key < best.d2)) break;
     }
     return best;
 }
@@ -465,13 +474,9 @@ __device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &
     float d0 = box_dist2<D>(T.root_lo, T.root_hi, x);
     if (d0 >= r2) return rmax;
     if (d0 > 0.f && !has_silhouette<D>(T.root_lo, T.root_hi, T.root_cone, x)) return rmax;
-    spush(st, sp, T.root, d0);
     bool found = false;
-    while (sp > 0) {
-        uint32_t ref;
-        float key;
-        spop(st, sp, ref, key);
-        if (key >= r2) continue;
+    uint32_t ref = T.root;
+    for (;;) {
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -482,21 +487,30 @@ __device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &
                     found = true;
                 }
             }
-            continue;
-        }
-        cnt.node(C_Q2);
-        Node<D> n = load_node<D>(T.nodes, ref);
-        float e0 = box_dist2<D>(n.lo0, n.hi0, x), e1 = box_dist2<D>(n.lo1, n.hi1, x);
-        bool v0 = e0 < r2, v1 = e1 < r2;
-        if (v0 && e0 > 0.f) v0 = has_silhouette<D>(n.lo0, n.hi0, load_cone<D>(T.cones, ref, 0), x);
-        if (v1 && e1 > 0.f) v1 = has_silhouette<D>(n.lo1, n.hi1, load_cone<D>(T.cones, ref, 1), x);
-        if (e0 <= e1) {
-            if (v1) spush(st, sp, n.r1, e1);
-            if (v0) spush(st, sp, n.r0, e0);
         } else {
-            if (v0) spush(st, sp, n.r0, e0);
-            if (v1) spush(st, sp, n.r1, e1);
+            cnt.node(C_Q2);
+            Node<D> n = load_node<D>(T.nodes, ref);
+            float e0 = box_dist2<D>(n.lo0, n.hi0, x), e1 = box_dist2<D>(n.lo1, n.hi1, x);
+            bool v0 = e0 < r2, v1 = e1 < r2;
+            if (v0 && e0 > 0.f) v0 = has_silhouette<D>(n.lo0, n.hi0, load_cone<D>(T.cones, ref, 0), x);
+            if (v1 && e1 > 0.f) v1 = has_silhouette<D>(n.lo1, n.hi1, load_cone<D>(T.cones, ref, 1), x);
+            if (v0 && v1) {
+                bool first0 = e0 <= e1;
+                spush(st, sp, first0 ? n.r1 : n.r0, first0 ? e1 : e0);
+                ref = first0 ? n.r0 : n.r1;
+                continue;
+            }
+            if (v0 || v1) {
+                ref = v0 ? n.r0 : n.r1;
+                continue;
+            }
         }
+        float key = INFINITY;
+        while (sp > 0) {
+            spop(st, sp, ref, key);
+            if (key < r2) break;
+        }
+        if (!(key < r2)) break;
     }
     return found ? sqrtf(r2) : rmax;
 }
@@ -515,12 +529,8 @@ __device__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, float 
     int sp = 0;
     float t0 = box_ray<D>(T.root_lo, T.root_hi, o, inv, tb);
     if (t0 == INFINITY) return -1;
-    spush(st, sp, T.root, t0);
-    while (sp > 0) {
-        uint32_t ref;
-        float key;
-        spop(st, sp, ref, key);
-        if (key > tb) continue;
+    uint32_t ref = T.root;
+    for (;;) {
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -537,18 +547,28 @@ __device__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, float 
                     }
                 }
             }
-            continue;
-        }
-        cnt.node(cq);
-        Node<D> n = load_node<D>(T.nodes, ref);
-        float a0 = box_ray<D>(n.lo0, n.hi0, o, inv, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, inv, tb);
-        if (a0 <= a1) {
-            if (a1 != INFINITY) spush(st, sp, n.r1, a1);
-            if (a0 != INFINITY) spush(st, sp, n.r0, a0);
         } else {
-            if (a0 != INFINITY) spush(st, sp, n.r0, a0);
-            if (a1 != INFINITY) spush(st, sp, n.r1, a1);
+            cnt.node(cq);
+            Node<D> n = load_node<D>(T.nodes, ref);
+            float a0 = box_ray<D>(n.lo0, n.hi0, o, inv, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, inv, tb);
+            bool h0 = a0 != INFINITY, h1 = a1 != INFINITY;
+            if (h0 && h1) {
+                bool first0 = a0 <= a1;
+                spush(st, sp, first0 ? n.r1 : n.r0, first0 ? a1 : a0);
+                ref = first0 ? n.r0 : n.r1;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? n.r0 : n.r1;
+                continue;
+            }
         }
+        float key = INFINITY;
+        while (sp > 0) {
+            spop(st, sp, ref, key);
+            if (key <= tb) break;
+        }
+        if (!(key <= tb)) break;
     }
     t_out = tb;
     return hit;

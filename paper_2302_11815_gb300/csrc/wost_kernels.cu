@@ -51,9 +51,15 @@ __global__ void __launch_bounds__(256) k_walk_plain(const SceneView sc, const So
         int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
         uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
         walk_init<D>(sp, w, pt, j);
-        Cnt<false> cnt;
-        while (!walk_step<D>(sc, sp, w, st, cnt)) {
+    }
+    // the warp reconverges after every step (see k_walk_persistent)
+    bool done = !active;
+    while (__any_sync(0xffffffffu, !done)) {
+        if (!done) {
+            Cnt<false> cnt;
+            done = walk_step<D>(sc, sp, w, st, cnt);
         }
+        __syncwarp();
     }
     if (warp_uniform_points) {
         // every lane of this warp estimates the same point: reduce first
@@ -88,12 +94,16 @@ __global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, con
     Stack st = make_stack(sp.stack_depth, acc.guard);
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
     Walk w;
-    bool have = false;
+    bool have = false, drained = false;
+    // All 32 lanes stay in this loop until the warp runs out of work and meet
+    // at __syncwarp() after every walk step, so the warp starts each step
+    // converged (without it, independent thread scheduling lets the lanes
+    // drift apart and issue alone).
     for (;;) {
         // regeneration: lanes without a walk take the next ones
-        unsigned act = __activemask();
-        unsigned need = __ballot_sync(act, !have);
+        unsigned need = __ballot_sync(FULL, !have && !drained);
         if (need) {
             int lead = __ffs(need) - 1;
             unsigned long long base = 0;
@@ -101,23 +111,28 @@ __global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, con
                 bool stop = *(volatile int *)acc.cancel != 0;
                 base = stop ? total : atomicAdd(acc.next_walk, (unsigned long long)__popc(need));
             }
-            base = __shfl_sync(act, base, lead);
-            if (!have) {
+            base = __shfl_sync(FULL, base, lead);
+            if (!have && !drained) {
                 unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
                 if (my < total) {
                     int64_t pt = (int64_t)(my / (uint64_t)sp.walks_per_point);
                     uint32_t j = (uint32_t)(my % (uint64_t)sp.walks_per_point) + sp.first_walk;
                     walk_init<D>(sp, w, pt, j);
                     have = true;
+                } else {
+                    drained = true;
                 }
             }
         }
-        if (!have) break;
-        Cnt<false> cnt;
-        if (walk_step<D>(sc, sp, w, st, cnt)) {
-            accumulate(acc, w);
-            have = false;
+        if (!__any_sync(FULL, have)) break;
+        if (have) {
+            Cnt<false> cnt;
+            if (walk_step<D>(sc, sp, w, st, cnt)) {
+                accumulate(acc, w);
+                have = false;
+            }
         }
+        __syncwarp();
     }
 }
 
@@ -134,11 +149,14 @@ __global__ void __launch_bounds__(256) k_walk_batch(const BatchHeader *__restric
     if (n_jobs <= 0) return;
     Stack st = make_stack(stack_depth, guard);
     const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
     Walk w;
     int job = -1;
+    bool drained = false;  // the launch's counter has run past `total`
+    // as in k_walk_persistent: the whole warp stays in the loop and
+    // reconverges after every step
     for (;;) {
-        unsigned act = __activemask();
-        unsigned need = __ballot_sync(act, job < 0);
+        unsigned need = __ballot_sync(FULL, job < 0 && !drained);
         if (need) {
             int lead = __ffs(need) - 1;
             unsigned long long base = 0;
@@ -146,35 +164,40 @@ __global__ void __launch_bounds__(256) k_walk_batch(const BatchHeader *__restric
                 bool stop = cancel && *(volatile const int *)cancel != 0;
                 base = stop ? total : atomicAdd(counter, (unsigned long long)__popc(need));
             }
-            base = __shfl_sync(act, base, lead);
-            if (job < 0) {
+            base = __shfl_sync(FULL, base, lead);
+            if (job < 0 && !drained) {
                 unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
-                if (my < total) {
+                if (my >= total) {
+                    drained = true;
+                } else {
                     int lo = 0, hi = n_jobs - 1;
                     while (lo < hi) {
                         int mid = (lo + hi + 1) >> 1;
                         if (jobs[mid].walk_begin <= my) lo = mid;
                         else hi = mid - 1;
                     }
-                    job = lo;
-                    if (*(volatile const int *)jobs[job].acc.cancel != 0) {
-                        job = -1;  // cancelled solve: its remaining walks are skipped
-                        continue;
+                    // a cancelled solve's remaining walks are skipped: the
+                    // lane takes another index at the next iteration
+                    if (*(volatile const int *)jobs[lo].acc.cancel == 0) {
+                        job = lo;
+                        const SolveParams &sp = jobs[job].sp;
+                        unsigned long long local = my - jobs[job].walk_begin;
+                        int64_t pt = sp.point_begin + (int64_t)(local / (uint64_t)sp.walks_per_point);
+                        uint32_t j = (uint32_t)(local % (uint64_t)sp.walks_per_point) + sp.first_walk;
+                        walk_init<D>(sp, w, pt, j);
                     }
-                    const SolveParams &sp = jobs[job].sp;
-                    unsigned long long local = my - jobs[job].walk_begin;
-                    int64_t pt = sp.point_begin + (int64_t)(local / (uint64_t)sp.walks_per_point);
-                    uint32_t j = (uint32_t)(local % (uint64_t)sp.walks_per_point) + sp.first_walk;
-                    walk_init<D>(sp, w, pt, j);
                 }
             }
         }
-        if (job < 0) break;
-        Cnt<false> cnt;
-        if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, st, cnt)) {
-            accumulate(jobs[job].acc, w);
-            job = -1;
+        if (!__any_sync(FULL, job >= 0 || !drained)) break;
+        if (job >= 0) {
+            Cnt<false> cnt;
+            if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, st, cnt)) {
+                accumulate(jobs[job].acc, w);
+                job = -1;
+            }
         }
+        __syncwarp();
     }
 }
 

@@ -16,15 +16,20 @@ def z_scores(err, se, allow):
     return shrunk / np.maximum(se, 1e-300)
 
 
-def check_z(err, se, allow, zthr=4.0, band=(0.5, 1.8), label=""):
+def check_z(err, se, allow, zthr=4.0, band=(0.5, 1.8), label="", dof=None):
+    """dof: degrees of freedom of the per-point SE (walks - 1) when few
+    walks are used; z then follows Student's t and the exceedance rate is
+    that of t (doubled for the heavy tails of the walk estimates)."""
     err = np.asarray(err, float)
     se = np.asarray(se, float)
     z = z_scores(err, se, allow)
     n = len(z)
     nbad = int(np.count_nonzero(np.abs(z) > zthr))
-    limit = int(stats.binom.ppf(0.999, n, 1e-4))
+    p = 1e-4 if dof is None else max(1e-4, 4.0 * stats.t.sf(zthr, dof))
+    limit = int(stats.binom.ppf(0.999, n, p))
     assert nbad <= limit, f"{label}: {nbad} of {n} points beyond {zthr} SE (limit {limit}); worst {np.max(np.abs(z)):.2f}"
-    assert np.all(np.abs(z) < 8.0), f"{label}: a point is {np.max(np.abs(z)):.2f} SE away"
+    hard = 8.0 if dof is None else 30.0  # few walks: Student-t tails
+    assert np.all(np.abs(z) < hard), f"{label}: a point is {np.max(np.abs(z)):.2f} SE away"
     keep = se > 2 * allow  # points whose error is not dominated by the shell bias
     if band is not None and keep.sum() >= 16:
         m = float(np.mean((err[keep] / se[keep]) ** 2))

@@ -1,6 +1,8 @@
 """The benchmark workload at full size, in the launch configuration bench.py
 times (persistent kernel, device-resident points): every point of the
-512 x 512 Koch-snowflake grid at 256 walks.
+512 x 512 Koch-snowflake grid, the full geometry and parameters, at 16 walks
+per point (a sixteenth of the benchmark's 256, which keeps the test near a
+minute: the full solve is about 1.1e11 walk steps).
 
   * whole grid: every walk accounted for, no guard fired, capped walks
     below 1e-3, per-point z scores against the exact solution (multiple-
@@ -28,11 +30,15 @@ def run():
     libbuild.build()
     wost.load()
     sc = scenes.config2()
+    sc["walks"] = WALKS
     S = wost.Scene(sc)
     res = wost.solve(S, torch.from_numpy(sc["points"]).cuda(), sc["walks"], sc["epsilon"], sc["r_min"],
                      sc["max_steps"], seed=777, kernel="persistent")
     S.close()
     return sc, res
+
+
+WALKS = 16
 
 
 def test_full_grid_accounting(run):
@@ -48,7 +54,8 @@ def test_full_grid_against_exact_solution(run):
     sc, res = run
     u = scenes.exact_u("sin2x_cos3y", (), sc["points"])
     L = np.max(np.linalg.norm(scenes.exact_grad("sin2x_cos3y", (), sc["vertices"].astype(float)), axis=1))
-    check_z(res["mean"] - u, res["se"], sc["epsilon"] * 1.05 * L, band=(0.5, 2.0), label="full grid")
+    check_z(res["mean"] - u, res["se"], sc["epsilon"] * 1.05 * L, band=(0.5, 2.0), label="full grid",
+            dof=WALKS - 1, zthr=6.0)
 
 
 def test_sampled_points_against_oracle(run):
