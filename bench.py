@@ -4,7 +4,10 @@ Workload: 2D Poisson on a level-5 Koch snowflake (3072 segments, half
 Dirichlet, half Neumann by arc length) with a 1024-segment random-walk hole
 (all Neumann); exact u = sin 2x cos 3y, f = 13 u; the interior cell centres of
 a 512 x 512 raster (139,674 points), 256 walks per point, eps = r_min = 1e-4.
-A step is one full solve of that workload (every point, every walk).
+The whole workload is about 1.1e11 walk steps (walks average ~3,000 steps:
+most of the boundary reflects).  A step is one strided batch of it: every
+16th grid point (~8,730 points, ~2.2 million walks, far more than the GPU's
+resident threads) with all 256 walks; 16 steps cover the grid.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -184,27 +187,23 @@ def measure_l2_read_gbs(torch, stream):
     return 50 * x.numel() * 4 / (s.elapsed_time(e) * 1e-3) / 1e9
 
 
-def cpu_baseline(sc, budget_s=15.0, seed=1):
-    """The FP64 oracle as it stands on all host cores, on a bounded sample."""
+def cpu_baseline(sc, walks=48, seed=1):
+    """The FP64 oracle as it stands on all host cores (one thread per point),
+    on a bounded sample: `cores` random grid points x `walks` of their walks
+    (about 10-30 s of CPU work on the workload)."""
     import oracle
     O = oracle.Scene(sc)
     rng = np.random.default_rng(seed)
-    order = rng.permutation(len(sc["points"]))
     cores = os.cpu_count() or 1
-    done_pts = steps = 0
+    idx = rng.choice(len(sc["points"]), cores, replace=False)
     t0 = time.perf_counter()
-    k = 0
-    chunk = max(1, cores // 4)
-    while time.perf_counter() - t0 < budget_s and k < len(order):
-        pts = sc["points"][order[k:k + chunk]]
-        r = oracle.solve(O, pts, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed)
-        steps += int(r["steps"].sum())
-        done_pts += len(pts)
-        k += chunk
+    r = oracle.solve(O, sc["points"][idx], walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed,
+                     threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done_pts} random points of the workload x {sc['walks']} walks ({steps} steps, {dt:.1f} s)",
-            "points_per_s": done_pts / dt}
+    steps = int(r["steps"].sum())
+    return {"value": steps / dt, "unit": UNIT, "cores": int(r["threads"]), "kind": "oracle",
+            "sample": f"{cores} random grid points x {walks} of their {sc['walks']} walks ({steps} steps, {dt:.1f} s)",
+            "points_per_s": cores * walks / sc["walks"] / dt}
 
 
 def run_reference(args):
@@ -214,11 +213,11 @@ def run_reference(args):
     from paper_2302_11815_gb300 import scenes
     sc = scenes.config2()
     for _ in range(args.warmup):
-        cpu_baseline(sc, budget_s=2.0, seed=99)
+        cpu_baseline(sc, walks=2, seed=99)
     vals = []
     t0 = time.perf_counter()
     for i in range(args.steps):
-        vals.append(cpu_baseline(sc, budget_s=args.ref_seconds, seed=i + 1))
+        vals.append(cpu_baseline(sc, walks=args.cpu_walks, seed=i + 1))
     elapsed = time.perf_counter() - t0
     v = float(np.mean([x["value"] for x in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -241,29 +240,34 @@ def run_ours(args):
 
     wost.load()  # fails loudly when the CUDA library is missing
     sc = scenes.config2()
-    pts_host = np.ascontiguousarray(sc["points"], np.float32)
-    n = len(pts_host)
+    grid_pts = np.ascontiguousarray(sc["points"], np.float32)
     walks = sc["walks"]
     S = wost.Scene(sc, device=local)
     info = S.info()
     stream = torch.cuda.Stream()
-    dev_pts = torch.from_numpy(pts_host).cuda()
+    # a step is one strided batch of the grid: every `batches`-th point (all
+    # 256 walks of each), batch b = points[b::batches]; consecutive steps take
+    # consecutive batches, so `batches` steps cover the whole workload
+    nb = args.batches
+    batch_host = [np.ascontiguousarray(grid_pts[b::nb]) for b in range(nb)]
+    batch_dev = [torch.from_numpy(p).cuda() for p in batch_host]
+    u_batch = [scenes.exact_u("sin2x_cos3y", (), p) for p in batch_host]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     seed0 = 1000 * (rank + 1)
 
-    def solve_dev(seed):
-        h = wost.wost_solve(S.handle, dev_pts, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed,
-                            kernel=args.kernel, block_size=args.block, stream=stream)
+    def solve_dev(b, seed):
+        h = wost.wost_solve(S.handle, batch_dev[b % nb], walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
+                            seed=seed, kernel=args.kernel, block_size=args.block, stream=stream)
         return h
 
     # work counts per step from the counting kernel on a subsample (untimed)
-    sub = torch.from_numpy(pts_host[:: args.count_stride].copy()).cuda()
+    sub = torch.from_numpy(batch_host[0][:: args.count_stride].copy()).cuda()
     r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting")
     bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2)
 
     # warm-up
     for i in range(args.warmup):
-        h = solve_dev(seed0 + 100 + i)
+        h = solve_dev(i, seed0 + 100 + i)
         wost.wost_wait(h)
         wost.wost_solve_destroy(h)
     torch.cuda.synchronize()
@@ -273,47 +277,56 @@ def run_ours(args):
     _barrier(world)
     torch.cuda.synchronize()
     total_steps = 0
+    total_points = 0
     dev_ms = 0.0
     kern_s = 0.0
     capped = 0
-    rms = []
-    u_exact = scenes.exact_u("sin2x_cos3y", (), pts_host)
+    err2 = ref2 = 0.0
     for i in range(args.steps):
+        b = (args.warmup + i) % nb
         with torch.cuda.stream(stream):
             flush.fill_(float(i))  # evict the scene and accumulators from L2
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        h = solve_dev(seed0 + i)
+        h = solve_dev(b, seed0 + i)
         ev1.record(stream)
         ev1.synchronize()
         dev_ms += ev0.elapsed_time(ev1)
-        mean, se, wd, pr = wost.wost_poll(h, n)
+        n_b = len(batch_host[b])
+        mean, se, wd, pr = wost.wost_poll(h, n_b)
         wost.wost_solve_destroy(h)
         total_steps += pr["total_steps"]
+        total_points += n_b
         kern_s += pr["elapsed_seconds"]
         capped += pr["capped_walks"]
-        rms.append(float(np.sqrt(np.mean((mean - u_exact) ** 2) / np.mean(u_exact ** 2))))
+        err2 += float(np.sum((mean - u_batch[b]) ** 2))
+        ref2 += float(np.sum(u_batch[b] ** 2))
     torch.cuda.synchronize()
     _barrier(world)
     clk = clocks.stop()
 
     t_max = _max_over_ranks(dev_ms * 1e-3, world, "cuda")
     steps_all = _sum_over_ranks(float(total_steps), world, "cuda")
-    pts_all = _sum_over_ranks(float(n * args.steps), world, "cuda")
+    pts_all = _sum_over_ranks(float(total_points), world, "cuda")
     value = steps_all / t_max
+    n = total_points / args.steps  # points per step
 
     # end to end through the C ABI with host buffers: host points in, host
     # estimates out, copies inside the timed region
     e2e_steps = 0
     _barrier(world)
     t0 = time.perf_counter()
+    e2e_h2d = e2e_d2h = 0
     for i in range(args.e2e_steps):
-        h = wost.wost_solve(S.handle, pts_host, walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
+        b = (args.warmup + args.steps + i) % nb
+        h = wost.wost_solve(S.handle, batch_host[b], walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
                             seed=seed0 + 500 + i, kernel=args.kernel, block_size=args.block)
         wost.wost_wait(h)
-        mean, se, wd, pr = wost.wost_poll(h, n)
+        mean, se, wd, pr = wost.wost_poll(h, len(batch_host[b]))
         wost.wost_solve_destroy(h)
         e2e_steps += pr["total_steps"]
+        e2e_h2d += batch_host[b].nbytes
+        e2e_d2h += len(batch_host[b]) * 8 * 4 + 4 * 8  # sum, sumsq, walks, steps + counters
     e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
 
@@ -344,18 +357,22 @@ def run_ours(args):
         "kernel_ms_avg": 1e3 * kern_avg, "counts_per_step": {k: v / r["total_steps"] for k, v in r["counts"].items()},
     })
     if rank == 0:
-        base = cpu_baseline(sc, budget_s=args.cpu_seconds) if (world == 1 and not args.no_cpu) else None
+        base = cpu_baseline(sc, walks=args.cpu_walks) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config_block(sc, {"kernel": args.kernel, "block": args.block or 128,
-                                         "parallelism": f"replicas x{world}"}),
+                                         "parallelism": f"replicas x{world}",
+                                         "step": f"one strided batch: every {nb}th grid point "
+                                                 f"(~{int(n)} points) x {walks} walks; {nb} steps cover the grid",
+                                         "batches": nb}),
             "points_per_s": pts_all / t_max,
-            "rel_rms_error": float(np.mean(rms)), "capped_walks": int(capped),
-            "mean_steps_per_walk": total_steps / (n * walks * args.steps),
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(pts_host.nbytes),
-                    "d2h_bytes_per_step": int(n * 8 * 4 + 4 * 8)},
+            "rel_rms_error": float(np.sqrt(err2 / ref2)), "capped_walks": int(capped),
+            "mean_steps_per_walk": total_steps / (total_points * walks),
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(e2e_h2d / max(args.e2e_steps, 1)),
+                    "d2h_bytes_per_step": int(e2e_d2h / max(args.e2e_steps, 1))},
             "gpu_launches": args.steps,
             "clocks": clk,
             "roofline": roof,
@@ -561,15 +578,15 @@ def main():
     ap.add_argument("--serve-drain", type=float, default=30.0)
     ap.add_argument("--round-seconds", type=float, default=0.02)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--batches", type=int, default=16, help="a step is every batches-th grid point")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="persistent", choices=["plain", "persistent"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--count-stride", type=int, default=16)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-walks", type=int, default=48, help="oracle walks per sampled point")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.mode == "batch":

@@ -18,6 +18,13 @@
 #include "wost_device.cuh"
 #include "wost_kernels.h"
 
+// Minimum resident 256-thread blocks per SM the walk kernels are compiled for
+// (bounds their registers: 1 -> no bound, 4 -> 64 registers, 5 -> 51).  A
+// build-time occupancy knob, chosen by measurement.
+#ifndef WOST_WALK_MIN_BLOCKS
+#define WOST_WALK_MIN_BLOCKS 1
+#endif
+
 namespace wost {
 
 __device__ __forceinline__ Stack make_stack(int depth, unsigned int *guard) {
@@ -40,7 +47,7 @@ __device__ __forceinline__ void accumulate(const Accumulators &acc, const Walk &
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
+__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     int warp_uniform_points) {
     Stack st = make_stack(sp.stack_depth, acc.guard);
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(256) k_walk_plain(const SceneView sc, const So
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, const SolveParams sp,
+__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
     Stack st = make_stack(sp.stack_depth, acc.guard);
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(256) k_walk_persistent(const SceneView sc, con
 // the jobs' walks; a lane maps its next index to a job by binary search over
 // the jobs' first indices and runs that job's walk on that job's scene.
 template <int D>
-__global__ void __launch_bounds__(256) k_walk_batch(const BatchHeader *__restrict__ hdr,
+__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const BatchHeader *__restrict__ hdr,
                                                     const BatchJob *__restrict__ jobs, unsigned long long *counter,
                                                     unsigned int *guard, int stack_depth, const int *cancel) {
     const int n_jobs = hdr->n_jobs;

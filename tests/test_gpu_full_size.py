@@ -1,14 +1,17 @@
 """The benchmark workload at full size, in the launch configuration bench.py
-times (persistent kernel, device-resident points): every point of the
-512 x 512 Koch-snowflake grid, the full geometry and parameters, at 16 walks
-per point (a sixteenth of the benchmark's 256, which keeps the test near a
-minute: the full solve is about 1.1e11 walk steps).
+times (persistent kernel, device-resident points, the full geometry and
+parameters of the 512 x 512 Koch-snowflake grid).
 
-  * whole grid: every walk accounted for, no guard fired, capped walks
-    below 1e-3, per-point z scores against the exact solution (multiple-
-    comparisons test of statcheck.py);
-  * sampled points: the FP64 oracle recomputes a few points with the same
-    random streams; per-point means agree within their standard errors.
+  * the whole grid (139,674 points) at 16 walks per point: every walk
+    accounted for, no guard fired, capped walks below 1e-3, and sampled
+    points recomputed by the FP64 oracle with the same random streams agree
+    within their standard errors;
+  * a 2% random subsample of the grid at the benchmark's 256 walks per point:
+    per-point z scores against the exact solution (multiple-comparisons test
+    of statcheck.py).  With only 16 walks that test is not valid near the
+    Dirichlet boundary, where most walks end within a few steps and the rare
+    walks that escape inward are often not sampled at all, so the sample
+    standard error understates the spread (the oracle shows the same).
 """
 import numpy as np
 import pytest
@@ -20,9 +23,11 @@ from statcheck import check_z
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+WALKS_GRID = 16
+
 
 @pytest.fixture(scope="module")
-def run():
+def setup():
     from paper_2302_11815_gb300 import build as libbuild
     from paper_2302_11815_gb300 import wost
 
@@ -30,43 +35,51 @@ def run():
     libbuild.build()
     wost.load()
     sc = scenes.config2()
-    sc["walks"] = WALKS
     S = wost.Scene(sc)
-    res = wost.solve(S, torch.from_numpy(sc["points"]).cuda(), sc["walks"], sc["epsilon"], sc["r_min"],
-                     sc["max_steps"], seed=777, kernel="persistent")
+    yield wost, sc, S
     S.close()
+
+
+@pytest.fixture(scope="module")
+def grid(setup):
+    wost, sc, S = setup
+    res = wost.solve(S, torch.from_numpy(sc["points"]).cuda(), WALKS_GRID, sc["epsilon"], sc["r_min"],
+                     sc["max_steps"], seed=777, kernel="persistent")
     return sc, res
 
 
-WALKS = 16
-
-
-def test_full_grid_accounting(run):
-    sc, res = run
+def test_full_grid_accounting(grid):
+    sc, res = grid
     n = len(sc["points"])
     assert n > 130000
     assert res["done"] == 1 and res["guard_flags"] == 0
-    assert int(res["walks"].min()) == sc["walks"] and int(res["walks"].sum()) == n * sc["walks"]
-    assert res["capped_walks"] <= 1e-3 * n * sc["walks"]
+    assert int(res["walks"].min()) == WALKS_GRID and int(res["walks"].sum()) == n * WALKS_GRID
+    assert res["capped_walks"] <= 1e-3 * n * WALKS_GRID
+    assert np.all(np.isfinite(res["mean"]))
 
 
-def test_full_grid_against_exact_solution(run):
-    sc, res = run
-    u = scenes.exact_u("sin2x_cos3y", (), sc["points"])
-    L = np.max(np.linalg.norm(scenes.exact_grad("sin2x_cos3y", (), sc["vertices"].astype(float)), axis=1))
-    check_z(res["mean"] - u, res["se"], sc["epsilon"] * 1.05 * L, band=(0.5, 2.0), label="full grid",
-            dof=WALKS - 1, zthr=6.0)
-
-
-def test_sampled_points_against_oracle(run):
-    sc, res = run
+def test_full_grid_sampled_points_against_oracle(grid):
+    sc, res = grid
     rng = np.random.default_rng(12)
-    idx = rng.choice(len(sc["points"]), 4, replace=False)
+    idx = rng.choice(len(sc["points"]), 6, replace=False)
     O = oracle.Scene(sc)
     for i in idx:
         # walk j of point i draws the counters (j, i, step, slot): the oracle
         # recomputes point i with the same streams as the full-grid launch
-        o = oracle.solve(O, sc["points"][i:i + 1], sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"],
+        o = oracle.solve(O, sc["points"][i:i + 1], WALKS_GRID, sc["epsilon"], sc["r_min"], sc["max_steps"],
                          seed=777, point_base=int(i))
         se = np.hypot(o["se"][0], res["se"][i])
-        assert abs(res["mean"][i] - o["mean"][0]) <= 4 * se, (i, res["mean"][i], o["mean"][0], se)
+        assert abs(res["mean"][i] - o["mean"][0]) <= 4 * se + 1e-6, (i, res["mean"][i], o["mean"][0], se)
+
+
+def test_subsample_at_benchmark_walks_against_exact(setup):
+    wost, sc, S = setup
+    rng = np.random.default_rng(13)
+    idx = np.sort(rng.choice(len(sc["points"]), len(sc["points"]) // 50, replace=False))
+    pts = sc["points"][idx]
+    res = wost.solve(S, torch.from_numpy(pts).cuda(), sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"],
+                     seed=778, kernel="persistent")
+    assert int(res["walks"].sum()) == len(pts) * sc["walks"]
+    u = scenes.exact_u("sin2x_cos3y", (), pts)
+    L = np.max(np.linalg.norm(scenes.exact_grad("sin2x_cos3y", (), sc["vertices"].astype(float)), axis=1))
+    check_z(res["mean"] - u, res["se"], sc["epsilon"] * 1.05 * L, band=(0.5, 2.0), label="subsample")
