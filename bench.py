@@ -38,6 +38,14 @@ WORKLOAD = "koch5_hole_poisson_2d_grid512_w256"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2: written between timed solves
 
 
+_T0 = time.perf_counter()
+
+
+def _log(msg):
+    """Progress on stderr (stdout carries only the JSON line)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def _config_block(sc, extra=None):
     cfg = {"workload": WORKLOAD, "n_points": int(len(sc["points"])), "walks_per_point": sc["walks"],
            "prims": int(len(sc["prims"])), "neumann_prims": int(sc["flags"].sum()), "epsilon": sc["epsilon"],
@@ -244,6 +252,7 @@ def run_ours(args):
     walks = sc["walks"]
     S = wost.Scene(sc, device=local)
     info = S.info()
+    _log(f"scene built: {info['n_dirichlet']} D + {info['n_neumann']} N prims, {len(grid_pts)} grid points")
     stream = torch.cuda.Stream()
     # a step is one strided batch of the grid: every `batches`-th point (all
     # 256 walks of each), batch b = points[b::batches]; consecutive steps take
@@ -265,6 +274,7 @@ def run_ours(args):
     r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting")
     bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2)
 
+    _log(f"work model: {r['total_steps']} steps counted, {bytes_step:.0f} B and {flops_step:.0f} flop per step")
     # warm-up
     for i in range(args.warmup):
         h = solve_dev(i, seed0 + 100 + i)
@@ -272,6 +282,7 @@ def run_ours(args):
         wost.wost_solve_destroy(h)
     torch.cuda.synchronize()
 
+    _log("warm-up done")
     clocks = ClockSampler(local)
     clocks.start()
     _barrier(world)
@@ -330,6 +341,7 @@ def run_ours(args):
     e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
 
+    _log(f"timed {args.steps} steps: {value:.3e} steps/s; e2e {e2e_val:.3e}")
     peaks, peak_src = _measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
@@ -357,6 +369,7 @@ def run_ours(args):
         "kernel_ms_avg": 1e3 * kern_avg, "counts_per_step": {k: v / r["total_steps"] for k, v in r["counts"].items()},
     })
     if rank == 0:
+        _log("oracle CPU baseline")
         base = cpu_baseline(sc, walks=args.cpu_walks) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -579,7 +592,7 @@ def main():
     ap.add_argument("--round-seconds", type=float, default=0.02)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--batches", type=int, default=16, help="a step is every batches-th grid point")
+    ap.add_argument("--batches", type=int, default=64, help="a step is every batches-th grid point")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="persistent", choices=["plain", "persistent"])

@@ -54,7 +54,9 @@ __device__ __forceinline__ P3 crossp(P3 a, P3 b) {
 // ---------------------------------------------------------------------------
 // Philox4x32-10
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+// One out-of-line copy: it is called from several places per step, and
+// inlining it at each one bloats the kernel past the instruction cache.
+__device__ __noinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
@@ -518,10 +520,13 @@ __device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &
 // ---------------------------------------------------------------------------
 // Q.3 ray against the Neumann boundary (closest hit / any hit)
 // ---------------------------------------------------------------------------
-template <int D, bool ANY, bool CN = false>
-__device__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, float &t_out, const Stack &st,
-                     Cnt<CN> &cnt) {
-    const int cq = ANY ? C_VIS : C_Q3;
+// any = true: stop at the first hit found (visibility test).  One out-of-line
+// copy serves both uses (code size, see philox10).
+template <int D, bool CN = false>
+__device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, bool any, float &t_out,
+                                  const Stack &st, Cnt<CN> &cnt) {
+    const int cq = any ? C_VIS : C_Q3;
+    const bool ANY = any;
     int hit = -1;
     if (T.root == WOST_EMPTY_REF) return -1;
     P3 inv = mk(1.f / v.x, 1.f / v.y, D == 3 ? 1.f / v.z : 0.f);
@@ -670,7 +675,7 @@ __device__ NSample q_sample(const TreeView &T, P3 x, float r, Stream &rng, Cnt<C
 // f = -Lap u)
 // ---------------------------------------------------------------------------
 template <int D>
-__device__ __forceinline__ float fn_u(int fn, const float *p, P3 x) {
+__device__ __noinline__ float fn_u(int fn, const float *p, P3 x) {
     switch (fn) {
     case 1: return expf(x.x) * cosf(x.y);
     case 2: return sinf(2.f * x.x) * cosf(3.f * x.y);
@@ -686,7 +691,7 @@ __device__ __forceinline__ float fn_u(int fn, const float *p, P3 x) {
     }
 }
 template <int D>
-__device__ __forceinline__ P3 fn_grad(int fn, const float *p, P3 x) {
+__device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
     switch (fn) {
     case 1: {
         float e = expf(x.x);
@@ -705,7 +710,7 @@ __device__ __forceinline__ P3 fn_grad(int fn, const float *p, P3 x) {
     }
 }
 template <int D>
-__device__ __forceinline__ float fn_neglap(int fn, P3 x) {
+__device__ __noinline__ float fn_neglap(int fn, P3 x) {
     if (fn == 2) return 13.f * sinf(2.f * x.x) * cosf(3.f * x.y);
     if (fn == 4) return 1.f;
     return 0.f;
@@ -723,7 +728,7 @@ __device__ __forceinline__ float corner_interp(const float4 *data, int rec, floa
 }
 
 template <int D>
-__device__ __forceinline__ float grid_eval(const FieldView &f, P3 y) {
+__device__ __noinline__ float grid_eval(const FieldView &f, P3 y) {
     float c[3] = {y.x, y.y, y.z};
     int i0[3] = {0, 0, 0};
     float fr[3] = {0.f, 0.f, 0.f};
@@ -775,8 +780,12 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     // previous step is at most dbound away (triangle inequality), which
     // prunes the search; the result is the exact closest point either way.
     float b = w.dbound * 1.0001f + 1e-6f;
-    Closest cl = q_closest<D, CN>(sc.D, w.x, st, cnt, b * b);
-    if (cl.rec < 0) cl = q_closest<D, CN>(sc.D, w.x, st, cnt);
+    Closest cl;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {  // one call site keeps the code small
+        cl = q_closest<D, CN>(sc.D, w.x, st, cnt, pass == 0 ? b * b : INFINITY);
+        if (cl.rec >= 0) break;
+    }
     w.steps += 1;
     float dD = sqrtf(cl.d2);
     if (dD < sp.epsilon || w.steps >= sp.max_steps) {
@@ -813,7 +822,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     if (w.onN && dotp<D>(w.n, v) > 0.f) v = v * -1.f;
     // first hit with the Neumann part of the star boundary (Q.3)
     float th;
-    int hrec = q_ray<D, false, CN>(sc.N, xq, v, r, -1, th, st, cnt);
+    int hrec = q_ray<D, CN>(sc.N, xq, v, r, -1, false, th, st, cnt);
     P3 p, np = mk(0.f, 0.f, 0.f);
     if (hrec >= 0) {
         p = xq + v * th;
@@ -835,7 +844,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
             // point of one primitive) has G = inf and measure zero: skipped
             if (dzl < r && dzl > 0.f) {
                 float tv;
-                int occ = q_ray<D, true, CN>(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, tv, st, cnt);
+                int occ = q_ray<D, CN>(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, true, tv, st, cnt);
                 if (occ < 0) {
                     float hv;
                     if (sc.h.kind == FIELD_ANALYTIC) {

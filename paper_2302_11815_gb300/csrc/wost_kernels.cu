@@ -320,7 +320,7 @@ __global__ void k_query_ray(const SceneView sc, int64_t n, const float *o, const
     if (skip && skip[i] >= 0 && skip[i] < n_ids) sk = rec_of_id[skip[i]];
     float tt;
     Cnt<false> cnt;
-    int r = q_ray<D, false>(sc.N, load_point<D>(o, i), load_point<D>(v, i), tmax[i], sk, tt, st, cnt);
+    int r = q_ray<D>(sc.N, load_point<D>(o, i), load_point<D>(v, i), tmax[i], sk, false, tt, st, cnt);
     hit[i] = r >= 0;
     t[i] = r >= 0 ? tt : tmax[i];
     prim[i] = r >= 0 ? __ldg(sc.N.ids + r) : -1;
