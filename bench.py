@@ -159,24 +159,27 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# algorithmic cost of one node visit / primitive test, per query (bytes read
-# from the memory hierarchy; FP32 operations with an FMA counted as 2)
-BYTES = {2: {"node": {"q1": 64, "q2": 96, "q3": 64, "q4": 64, "vis": 64},
-             "prim": {"q1": 24, "q2": 32, "q3": 16, "q4": 16, "vis": 16}},
-         3: {"node": {"q1": 64, "q2": 96, "q3": 64, "q4": 64, "vis": 64},
-             "prim": {"q1": 64, "q2": 48, "q3": 48, "q4": 48, "vis": 48}}}
-FLOPS = {2: {"node": {"q1": 24, "q2": 70, "q3": 34, "q4": 44, "vis": 34},
-             "prim": {"q1": 16, "q2": 12, "q3": 16, "q4": 22, "vis": 16}},
-         3: {"node": {"q1": 36, "q2": 90, "q3": 50, "q4": 60, "vis": 50},
-             "prim": {"q1": 45, "q2": 30, "q3": 34, "q4": 50, "vis": 34}}}
+# algorithmic cost of one node visit / primitive test, per query: bytes read
+# from the memory hierarchy and FP32 operations (an FMA counted as 2).  A node
+# visit reads one node record (plus its child cones in Q.2) of the layout the
+# kernels traverse, as reported in the scene info; its flops are per child
+# box test (2 children in a binary node, 8 in a wide one).
+PRIM_BYTES = {2: {"q1": 16, "q2": 32, "q3": 16, "q4": 16, "vis": 16},
+              3: {"q1": 48, "q2": 48, "q3": 48, "q4": 48, "vis": 48}}
+CHILD_FLOPS = {2: {"q1": 12, "q2": 35, "q3": 17, "q4": 22, "vis": 17},
+               3: {"q1": 18, "q2": 45, "q3": 25, "q4": 30, "vis": 25}}
+PRIM_FLOPS = {2: {"q1": 16, "q2": 12, "q3": 16, "q4": 22, "vis": 16},
+              3: {"q1": 45, "q2": 30, "q3": 34, "q4": 50, "vis": 34}}
 STEP_FLOPS = {2: 60, 3: 80}  # per-step bookkeeping: radius, direction, Green's function, source
 
 
-def work_per_step(counts, steps, dim):
+def work_per_step(counts, steps, dim, info):
+    children = 2 if info["lanes_per_walk"] == 1 else 8
     b = f = 0.0
     for q in ("q1", "q2", "q3", "q4", "vis"):
-        b += counts[f"{q}_nodes"] * BYTES[dim]["node"][q] + counts[f"{q}_prims"] * BYTES[dim]["prim"][q]
-        f += counts[f"{q}_nodes"] * FLOPS[dim]["node"][q] + counts[f"{q}_prims"] * FLOPS[dim]["prim"][q]
+        nb = info["node_bytes"] + (info["cone_bytes"] if q == "q2" else 0)
+        b += counts[f"{q}_nodes"] * nb + counts[f"{q}_prims"] * PRIM_BYTES[dim][q]
+        f += counts[f"{q}_nodes"] * children * CHILD_FLOPS[dim][q] + counts[f"{q}_prims"] * PRIM_FLOPS[dim][q]
     return b / steps, f / steps + STEP_FLOPS[dim]
 
 
@@ -254,100 +257,93 @@ def run_ours(args):
     info = S.info()
     _log(f"scene built: {info['n_dirichlet']} D + {info['n_neumann']} N prims, {len(grid_pts)} grid points")
     stream = torch.cuda.Stream()
-    # a step is one strided batch of the grid: every `batches`-th point (all
-    # 256 walks of each), batch b = points[b::batches]; consecutive steps take
-    # consecutive batches, so `batches` steps cover the whole workload
-    nb = args.batches
-    batch_host = [np.ascontiguousarray(grid_pts[b::nb]) for b in range(nb)]
-    batch_dev = [torch.from_numpy(p).cuda() for p in batch_host]
-    u_batch = [scenes.exact_u("sin2x_cos3y", (), p) for p in batch_host]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     seed0 = 1000 * (rank + 1)
 
-    def solve_dev(b, seed):
-        h = wost.wost_solve(S.handle, batch_dev[b % nb], walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
-                            seed=seed, kernel=args.kernel, block_size=args.block, stream=stream)
-        return h
-
     # work counts per step from the counting kernel on a subsample (untimed)
-    sub = torch.from_numpy(batch_host[0][:: args.count_stride].copy()).cuda()
-    r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting")
-    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2)
-
+    sub = torch.from_numpy(grid_pts[:: args.count_stride * 64].copy()).cuda()
+    r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting",
+                   timeout=600.0)
+    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2, info)
     _log(f"work model: {r['total_steps']} steps counted, {bytes_step:.0f} B and {flops_step:.0f} flop per step")
-    # warm-up
-    for i in range(args.warmup):
-        h = solve_dev(i, seed0 + 100 + i)
-        wost.wost_wait(h)
-        wost.wost_solve_destroy(h)
-    torch.cuda.synchronize()
 
-    _log("warm-up done")
+    # The job: every grid point x 256 walks (36 million walks, ~1.1e11 walk
+    # steps), device-resident, run as a resumable solve.  A bench step is
+    # one launch of it: every resident lane runs up to `iters` walk steps,
+    # drawing new walks as its walks end and carrying unfinished ones over.
+    pts_dev = torch.from_numpy(grid_pts).cuda()
+    job = wost.wost_solve(S.handle, pts_dev, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0,
+                          kernel="resumable", block_size=args.block, stream=stream)
+    n_all = len(grid_pts)
+
+    def steps_run():
+        return wost.wost_poll(job, n_all)[3]["steps_run"]
+
+    for i in range(args.warmup):
+        wost.wost_solve_advance(job, args.iters, stream)
+        stream.synchronize()
+    _log(f"warm-up done: {steps_run():.4e} steps run")
+
     clocks = ClockSampler(local)
     clocks.start()
     _barrier(world)
     torch.cuda.synchronize()
     total_steps = 0
-    total_points = 0
     dev_ms = 0.0
-    kern_s = 0.0
-    capped = 0
-    err2 = ref2 = 0.0
+    per_launch_ms = []
     for i in range(args.steps):
-        b = (args.warmup + i) % nb
         with torch.cuda.stream(stream):
-            flush.fill_(float(i))  # evict the scene and accumulators from L2
+            flush.fill_(float(i))  # evict the scene and the walk state from L2
+        s0 = steps_run()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        h = solve_dev(b, seed0 + i)
+        wost.wost_solve_advance(job, args.iters, stream)
         ev1.record(stream)
         ev1.synchronize()
-        dev_ms += ev0.elapsed_time(ev1)
-        n_b = len(batch_host[b])
-        mean, se, wd, pr = wost.wost_poll(h, n_b)
-        wost.wost_solve_destroy(h)
-        total_steps += pr["total_steps"]
-        total_points += n_b
-        kern_s += pr["elapsed_seconds"]
-        capped += pr["capped_walks"]
-        err2 += float(np.sum((mean - u_batch[b]) ** 2))
-        ref2 += float(np.sum(u_batch[b] ** 2))
+        ms = ev0.elapsed_time(ev1)
+        dev_ms += ms
+        per_launch_ms.append(ms)
+        total_steps += steps_run() - s0
     torch.cuda.synchronize()
     _barrier(world)
     clk = clocks.stop()
+    _, _, wd, pr = wost.wost_poll(job, n_all)
+    wost.wost_solve_destroy(job)
 
     t_max = _max_over_ranks(dev_ms * 1e-3, world, "cuda")
     steps_all = _sum_over_ranks(float(total_steps), world, "cuda")
-    pts_all = _sum_over_ranks(float(total_points), world, "cuda")
     value = steps_all / t_max
-    n = total_points / args.steps  # points per step
+    _log(f"timed {args.steps} launches: {value:.3e} steps/s ({dev_ms / args.steps:.0f} ms per launch)")
 
-    # end to end through the C ABI with host buffers: host points in, host
-    # estimates out, copies inside the timed region
-    e2e_steps = 0
+    # end to end through the C ABI with host buffers: a whole solve of every
+    # e2e_batches-th grid point (host points in, host estimates out, the
+    # copies and the tail of the longest walks inside the timed region)
     _barrier(world)
-    t0 = time.perf_counter()
+    e2e_steps = 0
     e2e_h2d = e2e_d2h = 0
+    t0 = time.perf_counter()
     for i in range(args.e2e_steps):
-        b = (args.warmup + args.steps + i) % nb
-        h = wost.wost_solve(S.handle, batch_host[b], walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
-                            seed=seed0 + 500 + i, kernel=args.kernel, block_size=args.block)
-        wost.wost_wait(h)
-        mean, se, wd, pr = wost.wost_poll(h, len(batch_host[b]))
+        pts_h = np.ascontiguousarray(grid_pts[i :: args.e2e_batches])
+        h = wost.wost_solve(S.handle, pts_h, walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
+                            seed=seed0 + 500 + i, kernel="resumable", block_size=args.block)
+        wost.wost_wait(h, 900.0)
+        mean, se, wdone, pe = wost.wost_poll(h, len(pts_h))
         wost.wost_solve_destroy(h)
-        e2e_steps += pr["total_steps"]
-        e2e_h2d += batch_host[b].nbytes
-        e2e_d2h += len(batch_host[b]) * 8 * 4 + 4 * 8  # sum, sumsq, walks, steps + counters
+        e2e_steps += pe["total_steps"]
+        e2e_h2d += pts_h.nbytes
+        e2e_d2h += len(pts_h) * 8 * 4 + 4 * 8 + 16  # sum, sumsq, walks, steps + counters
+        u = scenes.exact_u("sin2x_cos3y", (), pts_h)
+        e2e_rel = float(np.sqrt(np.sum((mean - u) ** 2) / np.sum(u ** 2)))
     e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
+    _log(f"e2e {e2e_val:.3e} steps/s")
 
-    _log(f"timed {args.steps} steps: {value:.3e} steps/s; e2e {e2e_val:.3e}")
     peaks, peak_src = _measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
     fp32_peak = 2 * 128 * sms * mhz * 1e6  # FMA = 2 flops, 128 FP32 lanes per SM
     l2_gbs = measure_l2_read_gbs(torch, stream)
-    kern_avg = kern_s / args.steps
+    kern_avg = dev_ms * 1e-3 / args.steps
     steps_per_launch = total_steps / args.steps
     achieved_b = bytes_step * steps_per_launch / kern_avg / 1e9
     achieved_f = flops_step * steps_per_launch / kern_avg / 1e12
@@ -360,7 +356,7 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": achieved_f, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved_f / (fp32_peak / 1e12), "traffic": None}
     roof.update({
-        "kernel": f"k_walk_{args.kernel}<2>", "unit_of_work": "walk step",
+        "kernel": "k_walk_resume<2>", "unit_of_work": "walk step",
         "bytes_per_step": bytes_step, "flops_per_step": flops_step,
         "l2_frac": achieved_b / l2_gbs, "l2_peak_gbs": l2_gbs, "l2_peak_src": "measured in this run (64 MiB resident read)",
         "fp32_frac": achieved_f / (fp32_peak / 1e12), "fp32_peak_tflops": fp32_peak / 1e12,
@@ -375,29 +371,35 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config_block(sc, {"kernel": args.kernel, "block": args.block or 128,
+            "config": _config_block(sc, {"kernel": "resumable", "block": args.block or 128,
                                          "parallelism": f"replicas x{world}",
-                                         "step": f"one strided batch: every {nb}th grid point "
-                                                 f"(~{int(n)} points) x {walks} walks; {nb} steps cover the grid",
-                                         "batches": nb}),
-            "points_per_s": pts_all / t_max,
-            "rel_rms_error": float(np.sqrt(err2 / ref2)), "capped_walks": int(capped),
-            "mean_steps_per_walk": total_steps / (total_points * walks),
+                                         "step": f"one launch of the whole-grid job ({n_all} points x {walks} walks):"
+                                                 f" every resident lane runs up to {args.iters} walk steps, drawing"
+                                                 f" new walks and carrying unfinished ones to the next launch",
+                                         "iters_per_launch": args.iters}),
+            "launch_ms": per_launch_ms,
+            "job_progress": {"walks_done": int(pr["walks_done"]), "steps_run": int(pr["steps_run"]),
+                             "launches": int(pr["launches"])},
             "e2e": {"value": e2e_val, "unit": UNIT,
                     "h2d_bytes_per_step": int(e2e_h2d / max(args.e2e_steps, 1)),
-                    "d2h_bytes_per_step": int(e2e_d2h / max(args.e2e_steps, 1))},
+                    "d2h_bytes_per_step": int(e2e_d2h / max(args.e2e_steps, 1)),
+                    "what": f"complete resumable solves of every {args.e2e_batches}th grid point x {walks} walks from"
+                            f" host memory (wost_solve + wost_wait + wost_poll), per solve",
+                    "rel_rms_error_vs_exact": e2e_rel},
             "gpu_launches": args.steps,
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": base,
             "scene": {k: info[k] for k in ("n_dirichlet", "n_neumann", "n_silhouette", "nodes_dirichlet",
                                            "nodes_neumann", "nodes_silhouette", "depth_dirichlet",
-                                           "depth_neumann", "depth_silhouette", "device_bytes", "build_seconds")},
+                                           "depth_neumann", "depth_silhouette", "device_bytes", "build_seconds",
+                                           "lanes_per_walk")},
         }
         print(json.dumps(line), flush=True)
     S.close()
     if world > 1:
         import torch.distributed as dist
+
         dist.destroy_process_group()
     return 0
 
@@ -576,9 +578,37 @@ def run_serve(args):
     return 0
 
 
+def run_profile_case(args):
+    """The benchmark job for a profiler: the whole-grid resumable solve,
+    `--warmup` launches then `--steps` launches of `--iters` walk steps per
+    lane (profile e.g. with -k regex:k_walk_resume -s <warmup> -c 1)."""
+    import torch
+
+    from paper_2302_11815_gb300 import scenes, wost
+
+    wost.load()
+    sc = scenes.config2()
+    S = wost.Scene(sc)
+    pts = torch.from_numpy(np.ascontiguousarray(sc["points"], np.float32)).cuda()
+    h = wost.wost_solve(S.handle, pts, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=5,
+                        kernel="resumable", block_size=args.block)
+    out = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        wost.wost_solve_advance(h, args.iters)
+        torch.cuda.synchronize()
+        out.append(time.perf_counter() - t0)
+    _, _, _, pr = wost.wost_poll(h, len(pts))
+    wost.wost_solve_destroy(h)
+    print(json.dumps({"mode": "profile", "points": len(pts), "launches": int(pr["launches"]),
+                      "iters": args.iters, "steps_run": int(pr["steps_run"]), "launch_s": out}), flush=True)
+    S.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve"])
+    ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "profile"])
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--batch-max-points", type=float, default=1e5)
     ap.add_argument("--batch-max-walks", type=float, default=1024)
@@ -591,8 +621,9 @@ def main():
     ap.add_argument("--serve-drain", type=float, default=30.0)
     ap.add_argument("--round-seconds", type=float, default=0.02)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--batches", type=int, default=64, help="a step is every batches-th grid point")
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--iters", type=int, default=4096, help="walk steps per lane per launch")
+    ap.add_argument("--e2e-batches", type=int, default=16, help="the e2e solve takes every n-th grid point")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--kernel", default="persistent", choices=["plain", "persistent"])
@@ -606,6 +637,8 @@ def main():
         sys.exit(run_batch(args))
     if args.mode == "serve":
         sys.exit(run_serve(args))
+    if args.mode == "profile":
+        sys.exit(run_profile_case(args))
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     sys.exit(run_reference(args) if args.impl == "reference" else run_ours(args))

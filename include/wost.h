@@ -118,6 +118,14 @@ typedef struct {
     int64_t device_bytes;      /* bytes of resident scene data               */
     double build_seconds;
     float bbox_lo[3], bbox_hi[3];
+    /* layout the walk kernels traverse: lanes per walk (1: binary trees, one
+     * lane per walk; 8: 8-wide trees, 8 cooperating lanes per walk), bytes
+     * read per node visit (node record; the silhouette tree adds its child
+     * cones), and the wide trees' node counts and depths */
+    int32_t lanes_per_walk;
+    int32_t node_bytes, cone_bytes;
+    int64_t wide_nodes_dirichlet, wide_nodes_neumann, wide_nodes_silhouette;
+    int32_t wide_depth_dirichlet, wide_depth_neumann, wide_depth_silhouette;
 } wost_scene_info;
 
 /* Builds the hierarchies on the host, uploads them, returns a handle.
@@ -143,8 +151,11 @@ typedef enum {
     WOST_KERNEL_PLAIN = 0,      /* one thread per walk, one launch             */
     WOST_KERNEL_PERSISTENT = 1, /* persistent lanes that regenerate finished
                                    walks from a work counter                   */
-    WOST_KERNEL_COUNTING = 2    /* the plain kernel plus per-query work
+    WOST_KERNEL_COUNTING = 2,   /* the plain kernel plus per-query work
                                    counters (see wost_solve_work_counts)       */
+    WOST_KERNEL_RESUMABLE = 3   /* persistent lanes over a fixed grid, run as a
+                                   sequence of bounded launches that carry
+                                   unfinished walks over (wost_solve_advance) */
 } wost_kernel;
 
 typedef struct {
@@ -172,6 +183,10 @@ typedef struct {
     uint64_t capped_walks;     /* walks stopped by max_steps                   */
     uint32_t guard_flags;      /* device guards: 1 = traversal stack overflow  */
     double elapsed_seconds;    /* from launch to completion (or to now)        */
+    uint64_t steps_run;        /* resumable solves: walk steps executed by the
+                                  completed launches, finished walks or not;
+                                  other kernels: total_steps                   */
+    uint64_t launches;         /* kernel launches of this solve so far          */
 } wost_progress;
 
 /* Starts a solve asynchronously on the stream and returns its handle.
@@ -179,6 +194,21 @@ typedef struct {
  * (n_points < 1, walks < 1, epsilon <= 0, r_min > epsilon, max_steps < 1,
  * a null points array), OUT_OF_MEMORY, CUDA. */
 wost_status wost_solve(wost_scene *scene, const wost_solve_desc *desc, wost_solve_handle **out);
+
+/* Resumable solves (desc->kernel = WOST_KERNEL_RESUMABLE): wost_solve
+ * allocates the solve's state, including one saved-walk slot per lane of a
+ * fixed resident grid, and launches nothing.  Each wost_solve_advance
+ * enqueues ONE launch on `stream` (NULL = the solve's stream) in which every
+ * lane runs at most `iterations` walk steps, drawing new walks as its walks
+ * end, and saves its unfinished walk for the next launch; the launches of a
+ * solve must run in order (one stream, or ordered by the caller).  No
+ * launch waits for the longest walks of the solve, which is what keeps
+ * the GPU full on workloads whose walk lengths have a long tail.  wost_wait
+ * on a resumable solve issues launches of 2048 iterations itself until
+ * every walk has finished.  The walks and estimates are those of the other
+ * kernels for the same seed.  Errors: INVALID_ARG (not a resumable solve,
+ * iterations < 1), CUDA. */
+wost_status wost_solve_advance(wost_solve_handle *solve, int32_t iterations, void *stream);
 
 /* Batching: starts n solves (any scenes of one device, any point counts, walk
  * counts and parameters) in ONE persistent launch per dimension present (2D

@@ -71,6 +71,7 @@ struct wost_scene {
     wost::HostScene host;
     wost::SceneView view{};
     wost::DevBuf bufs[16];
+    wost::DevBuf wbufs[6];  // wide layout: nodes and cones of the three trees
     wost::DevBuf n_rec_of_id;
     unsigned int *guard = nullptr;        // device guard word for query kernels
     wost::SceneView *view_dev = nullptr;  // device copy of `view` (batched launches)
@@ -104,6 +105,12 @@ struct wost_solve_handle {
     wost::DevBuf points, normals, onN;
     wost::DevBuf sum, sumsq, walks_done, steps, globals;  // globals: capped, next_walk, guard
     wost::DevBuf counts;                                   // counting kernel only
+    // resumable solves: saved-walk slots of the fixed grid, launch counters
+    // (steps_run u64, live u32), launches enqueued so far
+    wost::DevBuf slots, rstate;
+    int resume_blocks = 0;
+    uint64_t launches = 0;
+    bool resumable() const { return kernel == WOST_KERNEL_RESUMABLE; }
     int kernel = 0;
     int *cancel_host = nullptr;                            // mapped pinned
     int *cancel_dev = nullptr;

@@ -251,6 +251,84 @@ struct Flattener {
     }
 };
 
+// Collapses a binary tree into 8-wide nodes for group-cooperative traversal
+// (8 lanes test the 8 children of a node, or the up to 8 primitives of a
+// leaf, at once).  A binary subtree holding at most 8 primitives becomes one
+// wide leaf (its records are contiguous); otherwise the node's slots are
+// filled by repeatedly opening the internal child with the largest surface
+// measure.  Node layout (16 float4): per child c, q[2c] = (lo.xyz, ref bits),
+// q[2c+1] = (hi.xyz, 0); unused slots hold the empty reference.
+struct WideFlattener {
+    const std::vector<BNode> &bn;
+    int dim;
+    std::vector<float4> &out;
+    std::vector<std::vector<int>> slots;  // per wide node: binary node ids of its children
+    std::vector<int> wide_of;             // binary node -> wide node index (internal)
+    int depth = 0;
+
+    bool is_wide_leaf(int b) const { return bn[b].child[0] < 0 || bn[b].count <= WOST_WIDE; }
+    uint32_t ref_of(int b) const {
+        if (is_wide_leaf(b)) return leaf_ref((uint32_t)bn[b].first, (uint32_t)bn[b].count);
+        return (uint32_t)wide_of[b];
+    }
+    std::vector<int> open(int b) const {
+        std::vector<int> ch{bn[b].child[0], bn[b].child[1]};
+        while (ch.size() < (size_t)WOST_WIDE) {
+            int best = -1;
+            float area = -1;
+            for (size_t i = 0; i < ch.size(); ++i) {
+                if (is_wide_leaf(ch[i])) continue;
+                float a = area_measure(bn[ch[i]].lo, bn[ch[i]].hi, dim);
+                if (a > area) {
+                    area = a;
+                    best = (int)i;
+                }
+            }
+            if (best < 0) break;
+            int c = ch[best];
+            ch[best] = bn[c].child[0];
+            ch.insert(ch.begin() + best + 1, bn[c].child[1]);
+        }
+        return ch;
+    }
+    // returns the root reference
+    uint32_t run(int root) {
+        wide_of.assign(bn.size(), -1);
+        if (is_wide_leaf(root)) return ref_of(root);
+        // breadth-first numbering
+        std::vector<std::pair<int, int>> queue{{root, 1}};
+        wide_of[root] = 0;
+        int k = 1;
+        for (size_t i = 0; i < queue.size(); ++i) {
+            auto [b, lvl] = queue[i];
+            depth = std::max(depth, lvl);
+            std::vector<int> ch = open(b);
+            slots.push_back(ch);
+            for (int c : ch)
+                if (!is_wide_leaf(c)) {
+                    wide_of[c] = k++;
+                    queue.push_back({c, lvl + 1});
+                }
+        }
+        out.assign((size_t)k * 2 * WOST_WIDE, f4(INFINITY, INFINITY, INFINITY, ibits(WOST_EMPTY_REF)));
+        for (size_t i = 0; i < queue.size(); ++i) {
+            float4 *q = &out[(size_t)wide_of[queue[i].first] * 2 * WOST_WIDE];
+            const std::vector<int> &ch = slots[i];
+            for (int c = 0; c < WOST_WIDE; ++c) {
+                if (c >= (int)ch.size()) {
+                    q[2 * c] = f4(INFINITY, INFINITY, INFINITY, ibits(WOST_EMPTY_REF));
+                    q[2 * c + 1] = f4(-INFINITY, -INFINITY, -INFINITY, 0);
+                    continue;
+                }
+                const BNode &n = bn[ch[c]];
+                q[2 * c] = f4(n.lo[0], n.lo[1], n.lo[2], ibits(ref_of(ch[c])));
+                q[2 * c + 1] = f4(n.hi[0], n.hi[1], n.hi[2], 0);
+            }
+        }
+        return 0;
+    }
+};
+
 // Builds one tree over `items` (records 0..n-1) and returns the leaf order of
 // the records (perm[k] = record stored at position k).
 std::vector<int> build_tree(std::vector<Item> &items, int dim, int leaf, HostTree &t,
@@ -272,6 +350,12 @@ std::vector<int> build_tree(std::vector<Item> &items, int dim, int leaf, HostTre
     t.root = fl.ref_of(root);
     t.n_nodes = (int)(t.nodes.size() / 4);
     t.depth = b.max_depth_ + 1;
+    WideFlattener wf{b.nodes_, dim, t.wnodes, {}, {}};
+    t.wroot = wf.run(root);
+    t.wn_nodes = (int)(t.wnodes.size() / (2 * WOST_WIDE));
+    t.wdepth = wf.depth + 1;
+    t.wslots = wf.slots;
+    t.wide_of = wf.wide_of;
     for (int a = 0; a < 3; ++a) {
         t.root_lo[a] = b.nodes_[root].lo[a];
         t.root_hi[a] = b.nodes_[root].hi[a];
@@ -555,6 +639,12 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
                 S.S.cones[2 * fi + 1] = cf(cones[bn[b].child[1]]);
             }
             S.S.root_cone = cf(cones[root]);
+            // wide layout: the cone of every child slot
+            S.S.wcones.assign((size_t)S.S.wn_nodes * WOST_WIDE, f4(0, 0, 1, -1));
+            for (size_t i = 0; i < S.S.wslots.size(); ++i) {  // wide node i = i-th in breadth-first order
+                const std::vector<int> &ch = S.S.wslots[i];
+                for (size_t c = 0; c < ch.size(); ++c) S.S.wcones[i * WOST_WIDE + c] = cf(cones[ch[c]]);
+            }
         } else {
             S.S.root_cone = f4(0, 0, 1, -1);
         }

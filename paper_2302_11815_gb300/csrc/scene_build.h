@@ -18,6 +18,12 @@ struct HostTree {
     float root_lo[3] = {0, 0, 0}, root_hi[3] = {0, 0, 0};
     float4 root_cone = {0, 0, 1, -1};
     int n_prims = 0, n_nodes = 0, depth = 0;
+    // 8-wide layout of the same tree (same primitive records and order)
+    std::vector<float4> wnodes, wcones;
+    uint32_t wroot = WOST_EMPTY_REF;
+    int wn_nodes = 0, wdepth = 0;
+    std::vector<std::vector<int>> wslots;  // build-time only: binary children of each wide node
+    std::vector<int> wide_of;
 };
 
 struct HostScene {

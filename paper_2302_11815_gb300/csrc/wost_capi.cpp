@@ -82,6 +82,15 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
             V.n_prims = T.n_prims;
             V.n_nodes = T.n_nodes;
             V.depth = T.depth;
+            DevBuf *w = &s->wbufs[2 * t];
+            CK(upload(w[0], T.wnodes), "upload wide nodes");
+            CK(upload(w[1], T.wcones), "upload wide cones");
+            bytes += (int64_t)(w[0].bytes + w[1].bytes);
+            V.wnodes = (const float4 *)w[0].p;
+            V.wcones = (const float4 *)w[1].p;
+            V.wroot = T.wroot;
+            V.wn_nodes = T.wn_nodes;
+            V.wdepth = T.wdepth;
         }
         CK(upload(s->bufs[15], H.grid), "upload grid");
         bytes += (int64_t)s->bufs[15].bytes;
@@ -95,7 +104,14 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         s->view.h = H.h;
         s->view.f = H.f;
         s->view.f.grid = (const float *)s->bufs[15].p;
+#if WOST_TEAM == 1
+        // binary trees: one pending subtree per level
         s->stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
+#else
+        // 8-wide trees: at most 7 pending subtrees per level; odd, so that
+        // the teams of a warp start in different shared-memory banks
+        s->stack_depth = ((WOST_WIDE - 1) * std::max(H.D.wdepth, std::max(H.N.wdepth, H.S.wdepth)) + 1) | 1;
+#endif
         CK(cudaMalloc(&s->view_dev, sizeof(SceneView)), "cudaMalloc view");
         CK(cudaMemcpy(s->view_dev, &s->view, sizeof(SceneView), cudaMemcpyHostToDevice), "copy view");
         wost_scene_info &I = s->info;
@@ -110,6 +126,15 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         I.depth_dirichlet = H.D.depth;
         I.depth_neumann = H.N.depth;
         I.depth_silhouette = H.S.depth;
+        I.lanes_per_walk = WOST_TEAM;
+        I.node_bytes = WOST_TEAM == 1 ? (H.dim == 2 ? 48 : 64) : 2 * WOST_WIDE * 16;
+        I.cone_bytes = WOST_TEAM == 1 ? 32 : WOST_WIDE * 16;
+        I.wide_nodes_dirichlet = H.D.wn_nodes;
+        I.wide_nodes_neumann = H.N.wn_nodes;
+        I.wide_nodes_silhouette = H.S.wn_nodes;
+        I.wide_depth_dirichlet = H.D.wdepth;
+        I.wide_depth_neumann = H.N.wdepth;
+        I.wide_depth_silhouette = H.S.wdepth;
         I.device_bytes = bytes;
         I.build_seconds = H.build_seconds;
         for (int a = 0; a < 3; ++a) {
@@ -154,7 +179,8 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
     if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
         return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
-    if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING)
+    if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING &&
+        d->kernel != WOST_KERNEL_RESUMABLE)
         return fail(WOST_ERR_INVALID_ARG, "unknown kernel");
     int block = d->block_size ? d->block_size : (scene->tuned_block ? scene->tuned_block : 128);
     if (block < 32 || block > 256 || block % 32)
@@ -255,6 +281,17 @@ wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_h
         CK(cudaEventCreate(&h->ev_start), "cudaEventCreate");
         CK(cudaEventCreate(&h->ev_done), "cudaEventCreate");
         h->own_events = true;
+        if (d->kernel == WOST_KERNEL_RESUMABLE) {
+            // state only; the launches come from wost_solve_advance
+            CK(resume_grid(h->dim, h->block, h->sp.stack_depth, &h->resume_blocks), "occupancy");
+            CK(h->slots.alloc((size_t)resume_slots(h->block, h->resume_blocks) * 3 * sizeof(float4)), "cudaMalloc slots");
+            CK(h->rstate.alloc(16), "cudaMalloc counters");
+            CK(cudaMemsetAsync(h->slots.p, 0, h->slots.bytes, stream), "memset");
+            CK(cudaMemsetAsync(h->rstate.p, 0, 16, stream), "memset");
+            if ((st = wait_for_copies(stream)) != WOST_OK) return st;
+            *out = h.release();
+            return WOST_OK;
+        }
         if ((st = wait_for_copies(stream)) != WOST_OK) return st;
         const SolveParams &sp = h->sp;
         const Accumulators &acc = h->acc;
@@ -275,6 +312,7 @@ wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_h
         }
         if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
         CK(cudaEventRecord(h->ev_done, stream), "cudaEventRecord");
+        h->launches = 1;
         *out = h.release();
         return WOST_OK;
     } catch (const std::bad_alloc &) {
@@ -311,6 +349,7 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
             wost_status st = prepare_solve(scenes[i], &d, stream, hs[i].get());
             if (st != WOST_OK) return st;
             hs[i]->kernel = WOST_KERNEL_PERSISTENT;
+            hs[i]->launches = 1;
         }
         // jobs per dimension, in the caller's order
         std::vector<BatchJob> jobs[2];
@@ -375,9 +414,30 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
     }
 }
 
+// Resumable solve whose latest launch has completed: finished when that
+// launch saved no walk and no walk is left to draw (or the solve was
+// cancelled, which stops the drawing).
+static wost_status resumable_finished(wost_solve_handle *h, bool *finished) {
+    unsigned long long g[4] = {0, 0, 0, 0};
+    unsigned int st[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(g, h->globals.p, sizeof g, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+    CK(cudaMemcpyAsync(st, h->rstate.p, sizeof st, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+    CK(cudaStreamSynchronize(h->poll_stream), "poll sync");
+    const uint64_t total = (uint64_t)h->n_points * (uint64_t)h->walks;
+    *finished = st[2] == 0 && (g[1] >= total || *(volatile int *)h->cancel_host != 0);
+    return WOST_OK;
+}
+
 static wost_status check_done(wost_solve_handle *h) {
     if (h->done || !h->ev_done) return WOST_OK;  // engine requests are marked done by the engine
+    if (h->resumable() && h->launches == 0) return WOST_OK;  // nothing launched yet
     cudaError_t q = cudaEventQuery(h->ev_done);
+    if (q == cudaSuccess && h->resumable()) {
+        bool fin = false;
+        wost_status st = resumable_finished(h, &fin);
+        if (st != WOST_OK) return st;
+        if (!fin) return WOST_OK;
+    }
     if (q == cudaSuccess) {
         h->done = true;
         float ms = 0;
@@ -421,6 +481,9 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
         unsigned int bg = 0;
         if (h->batch_guard)
             CK(cudaMemcpyAsync(&bg, h->batch_guard, sizeof bg, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
+        unsigned long long rs[2] = {0, 0};
+        if (h->resumable())
+            CK(cudaMemcpyAsync(rs, h->rstate.p, sizeof rs, cudaMemcpyDeviceToHost, h->poll_stream), "poll copy");
         CK(cudaStreamSynchronize(h->poll_stream), "poll sync");
         uint64_t tw = 0, ts = 0;
         for (size_t i = 0; i < n; ++i) {
@@ -443,9 +506,41 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
             pr->guard_flags = (uint32_t)glob[2] | bg;
             pr->elapsed_seconds = was_done ? h->elapsed_done
                                            : std::chrono::duration<double>(std::chrono::steady_clock::now() - h->t_launch).count();
+            if (h->resumable() && h->launches == 0) pr->elapsed_seconds = 0;
+            pr->steps_run = h->resumable() ? rs[0] : ts;
+            pr->launches = h->launches;
         }
         if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
         return WOST_OK;
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
+// One launch of a resumable solve (caller holds h->mu).
+static wost_status advance_locked(wost_solve_handle *h, int iters, cudaStream_t s) {
+    if (h->launches == 0) {
+        h->t_launch = std::chrono::steady_clock::now();
+        CK(cudaEventRecord(h->ev_start, s), "cudaEventRecord");
+    }
+    unsigned int *live = (unsigned int *)((char *)h->rstate.p + 8);
+    CK(cudaMemsetAsync(live, 0, sizeof(unsigned int), s), "memset");
+    ResumeState rs{(float4 *)h->slots.p, (unsigned long long *)h->rstate.p, live};
+    CK(launch_walk_resume(h->scene->view, h->sp, h->acc, rs, iters, h->block, h->resume_blocks, s), "kernel launch");
+    CK(cudaEventRecord(h->ev_done, s), "cudaEventRecord");
+    h->launches++;
+    return WOST_OK;
+}
+
+wost_status wost_solve_advance(wost_solve_handle *h, int32_t iterations, void *stream) {
+    try {
+        if (!h) return fail(WOST_ERR_INVALID_ARG, "null solve");
+        if (!h->resumable()) return fail(WOST_ERR_INVALID_ARG, "solve was not started with the resumable kernel");
+        if (iterations < 1) return fail(WOST_ERR_INVALID_ARG, "iterations must be >= 1");
+        std::lock_guard<std::mutex> lk(h->mu);
+        CK(cudaSetDevice(h->device), "cudaSetDevice");
+        if (h->done) return WOST_OK;
+        return advance_locked(h, iterations, stream ? (cudaStream_t)stream : h->stream);
     } catch (const std::exception &e) {
         return fail(WOST_ERR_INTERNAL, e.what());
     }
@@ -461,6 +556,10 @@ wost_status wost_wait(wost_solve_handle *h, double timeout_s) {
             wost_status st = check_done(h);
             if (st != WOST_OK) return st;
             if (h->done) break;
+            // a resumable solve advances while its caller waits: the next
+            // launch as soon as the previous one has completed
+            if (h->resumable() && (h->launches == 0 || cudaEventQuery(h->ev_done) == cudaSuccess))
+                if ((st = advance_locked(h, 2048, h->stream)) != WOST_OK) return st;
         }
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (timeout_s >= 0 && el >= timeout_s) return fail(WOST_ERR_TIMEOUT, "solve not finished");

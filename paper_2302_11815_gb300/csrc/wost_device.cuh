@@ -102,6 +102,7 @@ template <bool ON>
 struct Cnt {
     __device__ __forceinline__ void node(int) {}
     __device__ __forceinline__ void prim(int) {}
+    __device__ __forceinline__ void prim_n(int, unsigned) {}
 };
 template <>
 struct Cnt<true> {
@@ -111,6 +112,7 @@ struct Cnt<true> {
     }
     __device__ __forceinline__ void node(int q) { ++nodes[q]; }
     __device__ __forceinline__ void prim(int q) { ++prims[q]; }
+    __device__ __forceinline__ void prim_n(int q, unsigned n) { prims[q] += n; }
 };
 
 // ---------------------------------------------------------------------------
@@ -772,10 +774,26 @@ struct Walk {
 
 __device__ __forceinline__ float maxabs3(P3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
 
+// Query policy over the binary trees: each lane answers its own walk's
+// queries with its own shared-memory stack.
+template <int D, bool CN>
+struct LaneQ {
+    Stack st;
+    Cnt<CN> &cnt;
+    __device__ Closest closest(const TreeView &T, P3 x, float bound2) { return q_closest<D, CN>(T, x, st, cnt, bound2); }
+    __device__ float silhouette(const TreeView &T, P3 x, float rmax) { return q_silhouette<D, CN>(T, x, rmax, st, cnt); }
+    __device__ int ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, bool any, float &t) {
+        return q_ray<D, CN>(T, o, v, tmax, skip, any, t, st, cnt);
+    }
+    __device__ NSample sample(const TreeView &T, P3 x, float r, Stream &rng) { return q_sample<D, CN>(T, x, r, rng, cnt); }
+};
+
 // One iteration of Alg. 1.  Returns true when the walk has terminated (its
-// estimate is then w.acc).
-template <int D, bool CN = false>
-__device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, const Stack &st, Cnt<CN> &cnt) {
+// estimate is then w.acc).  Q answers the geometric queries (LaneQ: one lane
+// per walk; GroupQ: 8 cooperating lanes per walk, every lane of the group
+// running this same code on the same walk).
+template <int D, class Q>
+__device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q &q) {
     // distance to the Dirichlet boundary (Q.1).  The closest point of the
     // previous step is at most dbound away (triangle inequality), which
     // prunes the search; the result is the exact closest point either way.
@@ -783,7 +801,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     Closest cl;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {  // one call site keeps the code small
-        cl = q_closest<D, CN>(sc.D, w.x, st, cnt, pass == 0 ? b * b : INFINITY);
+        cl = q.closest(sc.D, w.x, pass == 0 ? b * b : INFINITY);
         if (cl.rec >= 0) break;
     }
     w.steps += 1;
@@ -802,7 +820,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     float delta = sp.offset * (1.f + maxabs3(w.x));
     P3 xq = w.onN ? w.x - w.n * delta : w.x;
     // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
-    float dsil = q_silhouette<D, CN>(sc.S, xq, dD, st, cnt);
+    float dsil = q.silhouette(sc.S, xq, dD);
     float r = fminf(dD, fmaxf(sp.r_min, dsil));
     // direction: uniform, flipped into the hemisphere about -n_x on the boundary
     uint32_t k = (uint32_t)(w.steps - 1);
@@ -822,7 +840,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     if (w.onN && dotp<D>(w.n, v) > 0.f) v = v * -1.f;
     // first hit with the Neumann part of the star boundary (Q.3)
     float th;
-    int hrec = q_ray<D, CN>(sc.N, xq, v, r, -1, false, th, st, cnt);
+    int hrec = q.ray(sc.N, xq, v, r, -1, false, th);
     P3 p, np = mk(0.f, 0.f, 0.f);
     if (hrec >= 0) {
         p = xq + v * th;
@@ -836,7 +854,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
     if (!hzero && sc.N.root != WOST_EMPTY_REF) {
         Stream rng;
         rng.init(sp.key0, sp.key1, w.index, w.point, k);
-        NSample zs = q_sample<D, CN>(sc.N, w.x, r, rng, cnt);
+        NSample zs = q.sample(sc.N, w.x, r, rng);
         if (zs.rec >= 0 && zs.pdf > 0.f) {
             P3 dz = zs.z - w.x;
             float dzl = sqrtf(dotp<D>(dz, dz));
@@ -844,7 +862,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, c
             // point of one primitive) has G = inf and measure zero: skipped
             if (dzl < r && dzl > 0.f) {
                 float tv;
-                int occ = q_ray<D, CN>(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, true, tv, st, cnt);
+                int occ = q.ray(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, true, tv);
                 if (occ < 0) {
                     float hv;
                     if (sc.h.kind == FIELD_ANALYTIC) {

@@ -35,6 +35,12 @@
 #define WOST_EMPTY_REF 0xFFFFFFFFu
 #define WOST_MAX_LEAF 16
 #define WOST_MAX_DEPTH 60
+#define WOST_WIDE 8  // children per node of the wide layout (= lanes per walk team)
+// Lanes that cooperate on one walk: 1 = one lane per walk over the binary
+// trees, 8 = a team of 8 lanes per walk over the 8-wide trees.
+#ifndef WOST_TEAM
+#define WOST_TEAM 1
+#endif
 
 namespace wost {
 
@@ -63,6 +69,12 @@ struct TreeView {
     float root_lo[3], root_hi[3];
     float4 root_cone;       // S only
     int32_t n_prims, n_nodes, depth;
+    // 8-wide layout: 16 float4 per node (child c: (lo.xyz, ref), (hi.xyz, 0));
+    // S also has 8 float4 of child cones per node
+    const float4 *wnodes;
+    const float4 *wcones;
+    uint32_t wroot;
+    int32_t wn_nodes, wdepth;
 };
 
 struct SceneView {
@@ -84,7 +96,7 @@ struct SolveParams {
     uint32_t key0, key1;
     float offset;               // relative ray-origin offset on the boundary
     float vis_tmax;             // visibility ray end for the Neumann sample
-    int32_t stack_depth;        // shared-memory stack entries per thread
+    int32_t stack_depth;        // shared-memory stack entries per walk (thread or team)
 };
 
 struct Accumulators {
@@ -94,6 +106,16 @@ struct Accumulators {
     unsigned long long *next_walk;  // [1] work counter (persistent kernel)
     unsigned int *guard;            // [1] guard flags
     int *cancel;                    // [1] host-set cancel flag (mapped)
+};
+
+// Walks carried across the launches of a resumable solve: one slot per team
+// of the (fixed) launch grid, 3 float4: (x, acc), (n, dbound), (steps,
+// point, walk index, flags) with flags bit 0 = the slot holds a walk, bit 1
+// = on the Neumann boundary, bit 2 = capped.
+struct ResumeState {
+    float4 *slots;
+    unsigned long long *steps_run;  // [1] walk steps executed by all launches
+    unsigned int *live;             // [1] walks saved by the latest launch (cleared before it)
 };
 
 // Accumulators of one solve, for the per-solve summary kernel.

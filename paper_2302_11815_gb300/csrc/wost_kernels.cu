@@ -1,21 +1,29 @@
 // Walk kernels and batched query kernels (sm_103a).
 //
-//   k_walk_plain       one thread per walk, one launch per solve; a warp holds
-//                      its lanes until its longest walk ends.
-//   k_walk_persistent  one resident grid; each lane runs one walk step per
+// A walk is carried by a team of WOST_TEAM lanes (1: a lane per walk over
+// the binary trees; 8: a team per walk over the 8-wide trees, see
+// wost_group.cuh).  All lanes of a team hold the same walk state.
+//
+//   k_walk_plain       one team per walk, one launch per solve; a warp holds
+//                      its teams until its longest walk ends.
+//   k_walk_persistent  one resident grid; each team runs one walk step per
 //                      iteration and, when its walk ends, takes the next walk
 //                      from a global counter (warp ballot + one atomicAdd per
-//                      warp), so finished lanes are refilled at once.
-//   k_query_*          Q.1-Q.4 over arrays of queries (parity checks, reuse).
+//                      warp), so finished teams are refilled at once.
+//   k_walk_batch       the persistent kernel over many solves.
+//   k_query_*          Q.1-Q.4 over arrays of queries (parity checks, reuse),
+//                      through the same query code as the walks.
 //
-// Traversal stacks live in dynamic shared memory: stack_depth entries of
-// (node ref, key) per thread, laid out [entry][thread] so that a warp's
-// accesses fall in distinct banks.
+// Traversal stacks live in dynamic shared memory, stack_depth entries of
+// (node ref, key) per team: [entry][thread] for single lanes (a warp's
+// accesses fall in distinct banks), [team][entry] for teams of 8 (odd
+// stack_depth spreads the teams of a warp over the banks).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "wost_device.cuh"
+#include "wost_group.cuh"
 #include "wost_kernels.h"
 
 // Minimum resident 256-thread blocks per SM the walk kernels are compiled for
@@ -27,14 +35,43 @@
 
 namespace wost {
 
-__device__ __forceinline__ Stack make_stack(int depth, unsigned int *guard) {
+static_assert(WOST_TEAM == 1 || WOST_TEAM == WOST_WIDE, "a team is one lane or one lane per wide child");
+
+__device__ __forceinline__ Group make_team() {
+    Group g;
+    int lane = threadIdx.x & 31;
+    g.gl = lane & (WOST_TEAM - 1);
+    g.base = lane - g.gl;
+    g.mask = ((1u << WOST_TEAM) - 1u) << g.base;
+    return g;
+}
+
+#if WOST_TEAM == 1
+template <int D, bool CN>
+using WalkQ = LaneQ<D, CN>;
+#else
+template <int D, bool CN>
+using WalkQ = GroupQ<D, CN>;
+#endif
+
+// the query policy of this thread's team, with its shared-memory stack
+template <int D, bool CN>
+__device__ __forceinline__ WalkQ<D, CN> make_q(int depth, unsigned int *guard, Cnt<CN> &cnt) {
     extern __shared__ int2 smem_stack[];
-    Stack s;
-    s.base = smem_stack + threadIdx.x;
-    s.stride = blockDim.x;
-    s.cap = depth;
-    s.guard = guard;
-    return s;
+#if WOST_TEAM == 1
+    Stack s{smem_stack + threadIdx.x, (int)blockDim.x, depth, guard};
+    return LaneQ<D, CN>{s, cnt};
+#else
+    GStack s{smem_stack + (threadIdx.x / WOST_TEAM) * depth, depth, guard};
+    return GroupQ<D, CN>{make_team(), s, cnt};
+#endif
+}
+
+// host-set flag read once per team (every lane of a team must take the same
+// branch), null = not set
+__device__ __forceinline__ bool team_flag(const Group &g, const int *flag) {
+    int v = (g.leader() && flag) ? *(volatile const int *)flag : 0;
+    return __shfl_sync(g.mask, v, g.base) != 0;
 }
 
 __device__ __forceinline__ void accumulate(const Accumulators &acc, const Walk &w) {
@@ -49,10 +86,12 @@ __device__ __forceinline__ void accumulate(const Accumulators &acc, const Walk &
 template <int D>
 __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     int warp_uniform_points) {
-    Stack st = make_stack(sp.stack_depth, acc.guard);
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = gid < total && *(volatile int *)acc.cancel == 0;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    const bool active = gid < total && !team_flag(g, acc.cancel);
     Walk w;
     if (active) {
         int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
@@ -62,18 +101,16 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const 
     // the warp reconverges after every step (see k_walk_persistent)
     bool done = !active;
     while (__any_sync(0xffffffffu, !done)) {
-        if (!done) {
-            Cnt<false> cnt;
-            done = walk_step<D>(sc, sp, w, st, cnt);
-        }
+        if (!done) done = walk_step<D>(sc, sp, w, q);
         __syncwarp();
     }
+    const bool own = active && g.leader();  // one lane reports each walk
     if (warp_uniform_points) {
-        // every lane of this warp estimates the same point: reduce first
-        unsigned mask = __ballot_sync(0xffffffffu, active);
+        // every team of this warp estimates the same point: reduce first
+        unsigned mask = __ballot_sync(0xffffffffu, own);
         if (!mask) return;
-        double v = active ? (double)w.acc : 0.0, v2 = v * v;
-        unsigned long long s = active ? (unsigned long long)w.steps : 0ull, c = (active && w.capped) ? 1ull : 0ull;
+        double v = own ? (double)w.acc : 0.0, v2 = v * v;
+        unsigned long long s = own ? (unsigned long long)w.steps : 0ull, c = (own && w.capped) ? 1ull : 0ull;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -90,7 +127,7 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const 
             atomicAdd(acc.steps + pt, s);
             if (c) atomicAdd(acc.capped, c);
         }
-    } else if (active) {
+    } else if (own) {
         accumulate(acc, w);
     }
 }
@@ -98,19 +135,22 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const 
 template <int D>
 __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
-    Stack st = make_stack(sp.stack_depth, acc.guard);
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Walk w;
-    bool have = false, drained = false;
+    bool have = false, drained = false;  // uniform within a team
     // All 32 lanes stay in this loop until the warp runs out of work and meet
     // at __syncwarp() after every walk step, so the warp starts each step
     // converged (without it, independent thread scheduling lets the lanes
     // drift apart and issue alone).
     for (;;) {
-        // regeneration: lanes without a walk take the next ones
-        unsigned need = __ballot_sync(FULL, !have && !drained);
+        // regeneration: teams without a walk take the next ones (one ballot
+        // bit per team, on its leader)
+        unsigned need = __ballot_sync(FULL, g.leader() && !have && !drained);
         if (need) {
             int lead = __ffs(need) - 1;
             unsigned long long base = 0;
@@ -119,8 +159,8 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(c
                 base = stop ? total : atomicAdd(acc.next_walk, (unsigned long long)__popc(need));
             }
             base = __shfl_sync(FULL, base, lead);
-            if (!have && !drained) {
-                unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+            if ((need >> g.base) & 1u) {
+                unsigned long long my = base + __popc(need & ((1u << g.base) - 1u));
                 if (my < total) {
                     int64_t pt = (int64_t)(my / (uint64_t)sp.walks_per_point);
                     uint32_t j = (uint32_t)(my % (uint64_t)sp.walks_per_point) + sp.first_walk;
@@ -133,9 +173,8 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(c
         }
         if (!__any_sync(FULL, have)) break;
         if (have) {
-            Cnt<false> cnt;
-            if (walk_step<D>(sc, sp, w, st, cnt)) {
-                accumulate(acc, w);
+            if (walk_step<D>(sc, sp, w, q)) {
+                if (g.leader()) accumulate(acc, w);
                 have = false;
             }
         }
@@ -143,9 +182,99 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(c
     }
 }
 
+// Resumable persistent kernel: as k_walk_persistent, but each launch runs at
+// most `iters` loop iterations (one walk step each) and then saves the walk
+// its team holds into the team's slot; the next launch resumes it.  A solve
+// is a sequence of such launches over a fixed grid, so no launch waits for
+// the longest walks of the solve: their steps spill into later launches
+// while the rest of the grid keeps drawing new walks.
+template <int D>
+__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_resume(const SceneView sc, const SolveParams sp,
+                                                     const Accumulators acc, const ResumeState rs, int iters) {
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    const Group g = make_team();
+    const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    float4 *slot = rs.slots + 3 * (((size_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM);
+    Walk w;
+    bool have = false, drained = false;  // uniform within a team
+    {
+        float4 c = slot[2];
+        uint32_t flags = __float_as_uint(c.w);
+        if (flags & 1u) {
+            float4 a = slot[0], b = slot[1];
+            w.x = mk(a.x, a.y, a.z);
+            w.acc = a.w;
+            w.n = mk(b.x, b.y, b.z);
+            w.dbound = b.w;
+            w.steps = (int)__float_as_uint(c.x);
+            w.point = __float_as_uint(c.y);
+            w.index = __float_as_uint(c.z);
+            w.onN = (flags & 2u) != 0;
+            w.capped = (flags & 4u) != 0;
+            have = true;
+        }
+    }
+    unsigned long long ran = 0;
+    for (int it = 0; it < iters; ++it) {
+        unsigned need = __ballot_sync(FULL, g.leader() && !have && !drained);
+        if (need) {
+            int lead = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == lead) {
+                bool stop = *(volatile int *)acc.cancel != 0;
+                base = stop ? total : atomicAdd(acc.next_walk, (unsigned long long)__popc(need));
+            }
+            base = __shfl_sync(FULL, base, lead);
+            if ((need >> g.base) & 1u) {
+                unsigned long long my = base + __popc(need & ((1u << g.base) - 1u));
+                if (my < total) {
+                    int64_t pt = (int64_t)(my / (uint64_t)sp.walks_per_point);
+                    uint32_t j = (uint32_t)(my % (uint64_t)sp.walks_per_point) + sp.first_walk;
+                    walk_init<D>(sp, w, pt, j);
+                    have = true;
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(FULL, have)) break;
+        if (have) {
+            ++ran;
+            if (walk_step<D>(sc, sp, w, q)) {
+                if (g.leader()) accumulate(acc, w);
+                have = false;
+            }
+        }
+        __syncwarp();
+    }
+    if (g.leader()) {
+        if (have) {
+            uint32_t flags = 1u | (w.onN ? 2u : 0u) | (w.capped ? 4u : 0u);
+            slot[0] = make_float4(w.x.x, w.x.y, w.x.z, w.acc);
+            slot[1] = make_float4(w.n.x, w.n.y, w.n.z, w.dbound);
+            slot[2] = make_float4(__uint_as_float((uint32_t)w.steps), __uint_as_float(w.point),
+                                  __uint_as_float(w.index), __uint_as_float(flags));
+        } else {
+            slot[2] = make_float4(0.f, 0.f, 0.f, 0.f);  // flags 0: empty
+        }
+    }
+    // launch totals: steps run (one count per team) and walks saved
+    unsigned long long r = g.leader() ? ran : 0ull;
+    unsigned saved = __popc(__ballot_sync(FULL, g.leader() && have));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(FULL, r, o);
+    if (lane == 0) {
+        if (r) atomicAdd(rs.steps_run, r);
+        if (saved) atomicAdd(rs.live, saved);
+    }
+}
+
 // Batched persistent kernel: many solves (scenes, point sets, walk counts,
 // parameters) in one launch.  The walk index space is the concatenation of
-// the jobs' walks; a lane maps its next index to a job by binary search over
+// the jobs' walks; a team maps its next index to a job by binary search over
 // the jobs' first indices and runs that job's walk on that job's scene.
 template <int D>
 __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const BatchHeader *__restrict__ hdr,
@@ -154,7 +283,9 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const 
     const int n_jobs = hdr->n_jobs;
     const unsigned long long total = hdr->total;
     if (n_jobs <= 0) return;
-    Stack st = make_stack(stack_depth, guard);
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(stack_depth, guard, cnt);
+    const Group g = make_team();
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Walk w;
@@ -163,7 +294,7 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const 
     // as in k_walk_persistent: the whole warp stays in the loop and
     // reconverges after every step
     for (;;) {
-        unsigned need = __ballot_sync(FULL, job < 0 && !drained);
+        unsigned need = __ballot_sync(FULL, g.leader() && job < 0 && !drained);
         if (need) {
             int lead = __ffs(need) - 1;
             unsigned long long base = 0;
@@ -172,8 +303,8 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const 
                 base = stop ? total : atomicAdd(counter, (unsigned long long)__popc(need));
             }
             base = __shfl_sync(FULL, base, lead);
-            if (job < 0 && !drained) {
-                unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+            if ((need >> g.base) & 1u) {
+                unsigned long long my = base + __popc(need & ((1u << g.base) - 1u));
                 if (my >= total) {
                     drained = true;
                 } else {
@@ -184,8 +315,8 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const 
                         else hi = mid - 1;
                     }
                     // a cancelled solve's remaining walks are skipped: the
-                    // lane takes another index at the next iteration
-                    if (*(volatile const int *)jobs[lo].acc.cancel == 0) {
+                    // team takes another index at the next iteration
+                    if (!team_flag(g, jobs[lo].acc.cancel)) {
                         job = lo;
                         const SolveParams &sp = jobs[job].sp;
                         unsigned long long local = my - jobs[job].walk_begin;
@@ -198,9 +329,8 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const 
         }
         if (!__any_sync(FULL, job >= 0 || !drained)) break;
         if (job >= 0) {
-            Cnt<false> cnt;
-            if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, st, cnt)) {
-                accumulate(jobs[job].acc, w);
+            if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, q)) {
+                if (g.leader()) accumulate(jobs[job].acc, w);
                 job = -1;
             }
         }
@@ -264,34 +394,38 @@ cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_po
 template <int D>
 __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     unsigned long long *stats) {
-    Stack st = make_stack(sp.stack_depth, acc.guard);
+    Cnt<true> cnt;
+    auto q = make_q<D, true>(sp.stack_depth, acc.guard, cnt);
+    const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
     if (gid >= total) return;
     Walk w;
     int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
     uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
     walk_init<D>(sp, w, pt, j);
-    Cnt<true> cnt;
-    while (!walk_step<D, true>(sc, sp, w, st, cnt)) {
+    while (!walk_step<D>(sc, sp, w, q)) {
     }
+    if (!g.leader()) return;
     accumulate(acc, w);
-    for (int q = 0; q < C_NQ; ++q) {
-        atomicAdd(stats + q, (unsigned long long)cnt.nodes[q]);
-        atomicAdd(stats + C_NQ + q, (unsigned long long)cnt.prims[q]);
+    for (int c = 0; c < C_NQ; ++c) {
+        atomicAdd(stats + c, (unsigned long long)cnt.nodes[c]);
+        atomicAdd(stats + C_NQ + c, (unsigned long long)cnt.prims[c]);
     }
 }
 
 // ------------------------------- queries ---------------------------------
+// one team per query; the team's leader writes the answer
 template <int D>
 __global__ void k_query_closest(const SceneView sc, int64_t n, const float *pts, float *dist, float *closest,
                                 int32_t *prim, int depth, unsigned int *guard) {
-    Stack st = make_stack(depth, guard);
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(depth, guard, cnt);
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
     if (i >= n) return;
     P3 x = load_point<D>(pts, i);
-    Cnt<false> cnt;
-    Closest c = q_closest<D>(sc.D, x, st, cnt);
+    Closest c = q.closest(sc.D, x, INFINITY);
+    if (!make_team().leader()) return;
     dist[i] = sqrtf(c.d2);
     closest[D * i] = c.p.x;
     closest[D * i + 1] = c.p.y;
@@ -302,25 +436,27 @@ __global__ void k_query_closest(const SceneView sc, int64_t n, const float *pts,
 template <int D>
 __global__ void k_query_silhouette(const SceneView sc, int64_t n, const float *pts, const float *rmax, float *dist,
                                    int depth, unsigned int *guard) {
-    Stack st = make_stack(depth, guard);
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     Cnt<false> cnt;
-    dist[i] = q_silhouette<D>(sc.S, load_point<D>(pts, i), rmax[i], st, cnt);
+    auto q = make_q<D, false>(depth, guard, cnt);
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    if (i >= n) return;
+    float d = q.silhouette(sc.S, load_point<D>(pts, i), rmax[i]);
+    if (make_team().leader()) dist[i] = d;
 }
 
 template <int D>
 __global__ void k_query_ray(const SceneView sc, int64_t n, const float *o, const float *v, const float *tmax,
                             const int32_t *skip, const int32_t *rec_of_id, int64_t n_ids, int32_t *hit, float *t,
                             int32_t *prim, int depth, unsigned int *guard) {
-    Stack st = make_stack(depth, guard);
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(depth, guard, cnt);
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
     if (i >= n) return;
     int sk = -1;
     if (skip && skip[i] >= 0 && skip[i] < n_ids) sk = rec_of_id[skip[i]];
     float tt;
-    Cnt<false> cnt;
-    int r = q_ray<D>(sc.N, load_point<D>(o, i), load_point<D>(v, i), tmax[i], sk, false, tt, st, cnt);
+    int r = q.ray(sc.N, load_point<D>(o, i), load_point<D>(v, i), tmax[i], sk, false, tt);
+    if (!make_team().leader()) return;
     hit[i] = r >= 0;
     t[i] = r >= 0 ? tt : tmax[i];
     prim[i] = r >= 0 ? __ldg(sc.N.ids + r) : -1;
@@ -329,12 +465,14 @@ __global__ void k_query_ray(const SceneView sc, int64_t n, const float *o, const
 template <int D>
 __global__ void k_query_sample(const SceneView sc, int64_t n, const float *pts, const float *r, uint32_t k0,
                                uint32_t k1, uint32_t c1, uint32_t c2, float *z, float *pdf, int32_t *prim) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Cnt<false> cnt;
+    auto q = make_q<D, false>(0, nullptr, cnt);  // Q.4 keeps no stack
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
     if (i >= n) return;
     Stream rng;
     rng.init(k0, k1, (uint32_t)i, c1, c2);
-    Cnt<false> cnt;
-    NSample s = q_sample<D>(sc.N, load_point<D>(pts, i), r[i], rng, cnt);
+    NSample s = q.sample(sc.N, load_point<D>(pts, i), r[i], rng);
+    if (!make_team().leader()) return;
     z[D * i] = s.z.x;
     z[D * i + 1] = s.z.y;
     if (D == 3) z[D * i + 2] = s.z.z;
@@ -343,7 +481,7 @@ __global__ void k_query_sample(const SceneView sc, int64_t n, const float *pts, 
 }
 
 // ------------------------------- launchers --------------------------------
-static size_t smem_bytes(int depth, int block) { return (size_t)depth * block * sizeof(int2); }
+static size_t smem_bytes(int depth, int block) { return (size_t)depth * (block / WOST_TEAM) * sizeof(int2); }
 
 template <int D>
 static cudaError_t set_smem_attrs(size_t bytes) {
@@ -359,10 +497,10 @@ static cudaError_t set_smem_attrs(size_t bytes) {
 cudaError_t launch_walk_plain(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
                               cudaStream_t s) {
     uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    uint64_t grid = (total + block - 1) / block;
+    uint64_t grid = (total * WOST_TEAM + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
-    int uniform = (sp.walks_per_point % 32 == 0) && (block % 32 == 0);
+    int uniform = (sp.walks_per_point % (32 / WOST_TEAM) == 0) && (block % 32 == 0);
     cudaError_t e = sc.dim == 2 ? set_smem_attrs<2>(sm) : set_smem_attrs<3>(sm);
     if (e != cudaSuccess) return e;
     if (sc.dim == 2)
@@ -375,7 +513,7 @@ cudaError_t launch_walk_plain(const SceneView &sc, const SolveParams &sp, const 
 cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                               unsigned long long *stats, int block, cudaStream_t s) {
     uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    uint64_t grid = (total + block - 1) / block;
+    uint64_t grid = (total * WOST_TEAM + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
     if (sm > 48 * 1024) {
@@ -441,6 +579,34 @@ cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, c
     return cudaGetLastError();
 }
 
+cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t sm = smem_bytes(depth, block);
+    if (e == cudaSuccess && sm > 48 * 1024)
+        e = dim == 2 ? cudaFuncSetAttribute(k_walk_resume<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                     : cudaFuncSetAttribute(k_walk_resume<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_resume<2>, block, sm)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_resume<3>, block, sm);
+    if (e != cudaSuccess) return e;
+    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+int64_t resume_slots(int block, int blocks) { return (int64_t)blocks * (block / WOST_TEAM); }
+
+cudaError_t launch_walk_resume(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                               const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
+    size_t sm = smem_bytes(sp.stack_depth, block);
+    if (sc.dim == 2)
+        k_walk_resume<2><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
+    else
+        k_walk_resume<3><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
+    return cudaGetLastError();
+}
+
 static cudaError_t query_smem(const void *fn, size_t bytes) {
     if (bytes > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return cudaSuccess;
@@ -449,7 +615,7 @@ static cudaError_t query_smem(const void *fn, size_t bytes) {
 cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pts, float *dist, float *closest,
                                  int32_t *prim, int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n + block - 1) / block);
+    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_closest<2>, sm);
@@ -466,7 +632,7 @@ cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pt
 cudaError_t launch_query_silhouette(const SceneView &sc, int64_t n, const float *pts, const float *rmax, float *dist,
                                     int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n + block - 1) / block);
+    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_silhouette<2>, sm);
@@ -484,7 +650,7 @@ cudaError_t launch_query_ray(const SceneView &sc, int64_t n, const float *o, con
                              const int32_t *skip, const int32_t *rec_of_id, int64_t n_ids, int32_t *hit, float *t,
                              int32_t *prim, int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n + block - 1) / block);
+    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_ray<2>, sm);
@@ -502,7 +668,7 @@ cudaError_t launch_query_sample(const SceneView &sc, int64_t n, const float *pts
                                 uint32_t k1, uint32_t c1, uint32_t c2, float *z, float *pdf, int32_t *prim,
                                 cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n + block - 1) / block);
+    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
     if (sc.dim == 2)
         k_query_sample<2><<<grid, block, 0, s>>>(sc, n, pts, r, k0, k1, c1, c2, z, pdf, prim);
     else

@@ -26,7 +26,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "BUDGET", "CUDA", "TIMEOUT
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
 FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6}
 MEM_HOST, MEM_DEVICE = 0, 1
-KERNEL = {"plain": 0, "persistent": 1, "counting": 2}
+KERNEL = {"plain": 0, "persistent": 1, "counting": 2, "resumable": 3}
 COUNT_NAMES = ("q1", "q2", "q3", "q4", "vis")
 
 
@@ -54,7 +54,11 @@ class wost_scene_info(C.Structure):
                 ("n_silhouette", C.c_int64), ("n_dropped", C.c_int64), ("nodes_dirichlet", C.c_int64),
                 ("nodes_neumann", C.c_int64), ("nodes_silhouette", C.c_int64), ("depth_dirichlet", C.c_int32),
                 ("depth_neumann", C.c_int32), ("depth_silhouette", C.c_int32), ("device_bytes", C.c_int64),
-                ("build_seconds", C.c_double), ("bbox_lo", C.c_float * 3), ("bbox_hi", C.c_float * 3)]
+                ("build_seconds", C.c_double), ("bbox_lo", C.c_float * 3), ("bbox_hi", C.c_float * 3),
+                ("lanes_per_walk", C.c_int32), ("node_bytes", C.c_int32), ("cone_bytes", C.c_int32),
+                ("wide_nodes_dirichlet", C.c_int64), ("wide_nodes_neumann", C.c_int64),
+                ("wide_nodes_silhouette", C.c_int64), ("wide_depth_dirichlet", C.c_int32),
+                ("wide_depth_neumann", C.c_int32), ("wide_depth_silhouette", C.c_int32)]
 
 
 class wost_solve_desc(C.Structure):
@@ -67,7 +71,8 @@ class wost_solve_desc(C.Structure):
 
 class wost_progress(C.Structure):
     _fields_ = [("done", C.c_int32), ("walks_done", C.c_uint64), ("total_steps", C.c_uint64),
-                ("capped_walks", C.c_uint64), ("guard_flags", C.c_uint32), ("elapsed_seconds", C.c_double)]
+                ("capped_walks", C.c_uint64), ("guard_flags", C.c_uint32), ("elapsed_seconds", C.c_double),
+                ("steps_run", C.c_uint64), ("launches", C.c_uint64)]
 
 
 _SIGS = {
@@ -77,6 +82,7 @@ _SIGS = {
     "wost_solve": [C.c_void_p, C.POINTER(wost_solve_desc), C.POINTER(C.c_void_p)],
     "wost_poll": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(wost_progress)],
     "wost_wait": [C.c_void_p, C.c_double],
+    "wost_solve_advance": [C.c_void_p, C.c_int32, C.c_void_p],
     "wost_cancel": [C.c_void_p],
     "wost_solve_destroy": [C.c_void_p],
     "wost_solve_device_accumulators": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -353,6 +359,12 @@ def wost_poll(solve, n_points):
                             wd.ctypes.data_as(C.c_void_p), C.byref(pr)))
     prog = {k: getattr(pr, k) for k, _ in wost_progress._fields_}
     return mean, se, wd, prog
+
+
+def wost_solve_advance(solve, iterations=2048, stream=None):
+    """One launch of a resumable solve: every lane runs up to `iterations`
+    walk steps and saves its unfinished walk."""
+    _check(load().wost_solve_advance(solve, int(iterations), _stream_ptr(stream)))
 
 
 def wost_wait(solve, timeout_s=-1.0):

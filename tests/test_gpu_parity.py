@@ -253,6 +253,41 @@ def test_plain_and_persistent_give_the_same_walks(wost):
     assert a["total_steps"] == b["total_steps"]
 
 
+@pytest.mark.parametrize("iters", [1, 7, 2048])
+def test_resumable_gives_the_same_walks(wost, iters):
+    # walks carried across many short launches (1 and 7 steps per launch)
+    # end exactly as in one persistent launch
+    sc = scenes.config2(grid=24)
+    pts = sc["points"][:40]
+    a = _gpu_solve(wost, sc, pts, 64, 9, "persistent", eps=sc["epsilon"], max_steps=512)
+    S = wost.Scene(sc)
+    h = wost.wost_solve(S.handle, _dev(pts), 64, sc["epsilon"], sc["r_min"], 512, seed=9, kernel="resumable")
+    n_adv = 0
+    while True:
+        wost.wost_solve_advance(h, iters)
+        n_adv += 1
+        _, _, _, pr = wost.wost_poll(h, len(pts))
+        if pr["walks_done"] == len(pts) * 64 or n_adv > 100000:
+            break
+    wost.wost_wait(h)  # completion check: no walk left in a slot
+    mean, se, wd, pr = wost.wost_poll(h, len(pts))
+    wost.wost_solve_destroy(h)
+    S.close()
+    assert pr["done"] == 1 and pr["launches"] >= n_adv
+    assert int(wd.sum()) == len(pts) * 64
+    np.testing.assert_allclose(mean, a["mean"], rtol=1e-9, atol=1e-12)
+    assert pr["total_steps"] == a["total_steps"] and pr["capped_walks"] == a["capped_walks"]
+    assert pr["steps_run"] == pr["total_steps"]
+
+
+def test_resumable_wait_drives_the_launches(wost):
+    sc = scenes.config1(n_points=64)
+    a = _gpu_solve(wost, sc, sc["points"], 128, 4, "persistent")
+    b = _gpu_solve(wost, sc, sc["points"], 128, 4, "resumable")
+    np.testing.assert_allclose(a["mean"], b["mean"], rtol=1e-9, atol=1e-12)
+    assert a["total_steps"] == b["total_steps"] and b["launches"] >= 1
+
+
 def test_host_and_device_inputs_agree(wost):
     sc = scenes.config1(n_points=32)
     a = _gpu_solve(wost, sc, sc["points"], 64, 2, device_points=True)
