@@ -181,7 +181,8 @@ typedef struct {
     uint64_t walks_done;       /* walks accumulated so far                     */
     uint64_t total_steps;      /* walk steps (each Q.1 evaluation is a step)   */
     uint64_t capped_walks;     /* walks stopped by max_steps                   */
-    uint32_t guard_flags;      /* device guards: 1 = traversal stack overflow  */
+    uint32_t guard_flags;      /* device guards: 1 = traversal stack overflow,
+                                  2 = a traversal exceeded its visit limit     */
     double elapsed_seconds;    /* from launch to completion (or to now)        */
     uint64_t steps_run;        /* resumable solves: walk steps executed by the
                                   completed launches, finished walks or not;

@@ -46,6 +46,11 @@
  *   R7 2D source radius t = R sqrt(U1 U2); 3D t = R (1/2 + sin(asin(2U-1)/3))
  *      (inverse CDF of Beta(2,2)); both are the normalised G_B of App. A.
  *   R12 a Neumann sample at distance exactly 0 from x contributes nothing.
+ *   R13 a walk whose position lies outside the bounding box of the
+ *      boundary grown by its largest side on every side (or is not finite)
+ *      has left the domain: it ends like a capped walk (R5).  Exact
+ *      arithmetic never gets there; single precision can, through a gap
+ *      between two primitives.
  */
 #include "wost_oracle.h"
 
@@ -222,6 +227,7 @@ struct orc_scene {
     int32_t *tprims;
     orc_field g, h, f;
     double *gv, *hv, *fv;
+    double blo[3], bhi[3]; /* R13: grown bounding box of the vertices */
 };
 
 static V3 vert(const orc_scene *s, int i) { return s->V[i]; }
@@ -416,7 +422,29 @@ orc_scene *orc_scene_new(int dim, int nv, const double *vertices, int np, const 
     s->hv = copy_vals(h, field_len(s, h));
     s->fv = copy_vals(f, field_len(s, f));
     s->g.values = s->gv; s->h.values = s->hv; s->f.values = s->fv;
+    /* R13: bounding box of the vertices grown by its largest side */
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < nv; ++i) {
+        double c[3] = {s->V[i].x, s->V[i].y, s->V[i].z};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], c[a]);
+            hi[a] = fmax(hi[a], c[a]);
+        }
+    }
+    double m = 0.0;
+    for (int a = 0; a < dim; ++a) m = fmax(m, hi[a] - lo[a]);
+    for (int a = 0; a < 3; ++a) {
+        s->blo[a] = lo[a] - m;
+        s->bhi[a] = hi[a] + m;
+    }
     return s;
+}
+
+/* R13: inside the grown bounding box (false for a non-finite position) */
+static int in_bounds(const orc_scene *s, V3 x) {
+    int in = x.x >= s->blo[0] && x.x <= s->bhi[0] && x.y >= s->blo[1] && x.y <= s->bhi[1];
+    if (s->dim == 3) in = in && x.z >= s->blo[2] && x.z <= s->bhi[2];
+    return in;
 }
 
 void orc_scene_free(orc_scene *s) {
@@ -812,10 +840,12 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
         V3 xbar = mk(0, 0, 0);
         int primD;
         double bary[3] = {0, 0, 0};
+        int lost = !in_bounds(s, x); /* R13 */
         double dD = q_closest_dirichlet(s, x, &xbar, &primD, bary);
-        int last = dD < pr->epsilon || k + 1 >= pr->max_steps;
+        int last = dD < pr->epsilon || k + 1 >= pr->max_steps || lost;
         if (last) {
-            /* epsilon shell: return g at the closest point; R5: same at the cap */
+            /* epsilon shell: return g at the closest point; R5, R13: same at
+             * the cap and outside the grown bounding box */
             if (dD >= pr->epsilon) *capped_out = 1;
             if (primD >= 0) acc += eval_g(s, primD, xbar, bary);
             if (rows && *nrows < max_rows) {

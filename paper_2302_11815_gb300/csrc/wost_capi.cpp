@@ -104,6 +104,14 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         s->view.h = H.h;
         s->view.f = H.f;
         s->view.f.grid = (const float *)s->bufs[15].p;
+        {
+            float m = 0.f;
+            for (int a = 0; a < H.dim; ++a) m = std::max(m, H.hi[a] - H.lo[a]);
+            for (int a = 0; a < 3; ++a) {
+                s->view.out_lo[a] = H.lo[a] - m;
+                s->view.out_hi[a] = H.hi[a] + m;
+            }
+        }
 #if WOST_TEAM == 1
         // binary trees: one pending subtree per level
         s->stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
@@ -510,7 +518,7 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
             pr->steps_run = h->resumable() ? rs[0] : ts;
             pr->launches = h->launches;
         }
-        if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+        if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow or visit limit)");
         return WOST_OK;
     } catch (const std::exception &e) {
         return fail(WOST_ERR_INTERNAL, e.what());
@@ -574,7 +582,7 @@ wost_status wost_wait(wost_solve_handle *h, double timeout_s) {
     CK(cudaMemcpy(glob, h->globals.p, sizeof glob, cudaMemcpyDeviceToHost), "copy guard");
     unsigned int bg = 0;
     if (h->batch_guard) CK(cudaMemcpy(&bg, h->batch_guard, sizeof bg, cudaMemcpyDeviceToHost), "copy guard");
-    if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+    if ((uint32_t)glob[2] | bg) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow or visit limit)");
     if (*(volatile int *)h->cancel_host) return fail(WOST_ERR_CANCELLED, "solve was cancelled");
     return WOST_OK;
 }
@@ -624,7 +632,7 @@ static wost_status query_epilogue(wost_scene *s, cudaError_t e, cudaStream_t st)
     unsigned int g = 0;
     CK(cudaMemcpyAsync(&g, s->guard, sizeof g, cudaMemcpyDeviceToHost, st), "copy guard");
     CK(cudaStreamSynchronize(st), "query sync");
-    if (g) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow)");
+    if (g) return fail(WOST_ERR_INTERNAL, "device guard fired (traversal stack overflow or visit limit)");
     return WOST_OK;
 }
 

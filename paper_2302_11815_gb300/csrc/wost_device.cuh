@@ -138,6 +138,15 @@ __device__ __forceinline__ void spop(const Stack &s, int &sp, uint32_t &ref, flo
     key = __int_as_float(e.y);
 }
 
+// A traversal visits every node and leaf at most once: more visits than
+// that (2 n_nodes + 1) mean a corrupt tree.  The traversal then stops and
+// records guard bit 2 (guard may be null: not recorded) instead of running on.
+__device__ __forceinline__ bool over_visit_limit(unsigned &visits, int n_nodes, unsigned int *guard) {
+    if (++visits <= 2u * (unsigned)n_nodes + 8u) return false;
+    if (guard) atomicOr(guard, 2u);
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // nodes
 // ---------------------------------------------------------------------------
@@ -308,9 +317,17 @@ __device__ __forceinline__ float prim_area(const Prim<D> &p) {
     }
 }
 
-// ray o + t v against a primitive, 0 < t <= tmax
+// ray o + t v against a primitive, 0 < t <= tmax.  The edge tests accept a
+// margin `tol` in the segment parameter / barycentric coordinates.  Q.3 uses
+// kEdgeTol: with exact arithmetic a ray through a vertex shared by two
+// primitives hits both, in single precision it can miss both (rounding
+// errors of order 1e-5 in these parameters for the short segments of the
+// workloads), and the walk would cross the boundary through that gap.  The
+// visibility test uses no margin (a margin there would hide samples next to
+// a vertex).
+constexpr float kEdgeTol = 1e-4f;
 template <int D>
-__device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tmax, float &t) {
+__device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tmax, float &t, float tol) {
     if constexpr (D == 2) {
         P3 e = p.b - p.a, ao = p.a - o;
         float den = v.x * e.y - v.y * e.x;
@@ -318,7 +335,7 @@ __device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tma
         float inv = 1.f / den;
         float tt = (ao.x * e.y - ao.y * e.x) * inv;
         float u = (ao.x * v.y - ao.y * v.x) * inv;
-        if (u < 0.f || u > 1.f || !(tt > 0.f) || tt > tmax) return false;
+        if (u < -tol || u > 1.f + tol || !(tt > 0.f) || tt > tmax) return false;
         t = tt;
         return true;
     } else {
@@ -329,10 +346,10 @@ __device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tma
         float inv = 1.f / det;
         P3 tv = o - p.a;
         float u = dotp<3>(tv, pv) * inv;
-        if (u < 0.f || u > 1.f) return false;
+        if (u < -tol || u > 1.f + tol) return false;
         P3 qv = crossp(tv, e1);
         float w = dotp<3>(v, qv) * inv;
-        if (w < 0.f || u + w > 1.f) return false;
+        if (w < -tol || u + w > 1.f + tol) return false;
         float tt = dotp<3>(e2, qv) * inv;
         if (!(tt > 0.f) || tt > tmax) return false;
         t = tt;
@@ -366,7 +383,9 @@ __device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &
     int sp = 0;
     uint32_t ref = T.root;
     if (box_dist2<D>(T.root_lo, T.root_hi, x) >= best.d2) return best;
+    unsigned visits = 0;
     for (;;) {
+        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -480,7 +499,9 @@ __device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &
     if (d0 > 0.f && !has_silhouette<D>(T.root_lo, T.root_hi, T.root_cone, x)) return rmax;
     bool found = false;
     uint32_t ref = T.root;
+    unsigned visits = 0;
     for (;;) {
+        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -529,6 +550,7 @@ __device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int
                                   const Stack &st, Cnt<CN> &cnt) {
     const int cq = any ? C_VIS : C_Q3;
     const bool ANY = any;
+    const float tol = any ? 0.f : kEdgeTol;
     int hit = -1;
     if (T.root == WOST_EMPTY_REF) return -1;
     P3 inv = mk(1.f / v.x, 1.f / v.y, D == 3 ? 1.f / v.z : 0.f);
@@ -537,7 +559,9 @@ __device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int
     float t0 = box_ray<D>(T.root_lo, T.root_hi, o, inv, tb);
     if (t0 == INFINITY) return -1;
     uint32_t ref = T.root;
+    unsigned visits = 0;
     for (;;) {
+        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -545,7 +569,7 @@ __device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int
                 cnt.prim(cq);
                 Prim<D> p = load_prim<D>(T.prims, k);
                 float t;
-                if (prim_ray<D>(p, o, v, tb, t)) {
+                if (prim_ray<D>(p, o, v, tb, t, tol)) {
                     tb = t;
                     hit = (int)k;
                     if (ANY) {
@@ -604,8 +628,10 @@ __device__ NSample q_sample(const TreeView &T, P3 x, float r, Stream &rng, Cnt<C
     uint32_t ref = T.root;
     float pdf = 1.f;
     // Alg. 6: one random child among those whose box meets the ball, weighted
-    // by proximity of the box centre
-    while (!is_leaf(ref)) {
+    // by proximity of the box centre (a descent longer than the tree is deep
+    // means a corrupt tree: no sample)
+    for (int level = 0; !is_leaf(ref); ++level) {
+        if (level > WOST_MAX_DEPTH) return out;
         cnt.node(C_Q4);
         Node<D> n = load_node<D>(T.nodes, ref);
         float w0 = 0.f, w1 = 0.f;
@@ -792,8 +818,19 @@ struct LaneQ {
 // estimate is then w.acc).  Q answers the geometric queries (LaneQ: one lane
 // per walk; GroupQ: 8 cooperating lanes per walk, every lane of the group
 // running this same code on the same walk).
+// R13: inside the grown bounding box (false for a non-finite position)
+template <int D>
+__device__ __forceinline__ bool in_bounds(const SceneView &sc, P3 x) {
+    bool in = x.x >= sc.out_lo[0] && x.x <= sc.out_hi[0] && x.y >= sc.out_lo[1] && x.y <= sc.out_hi[1];
+    if constexpr (D == 3) in = in && x.z >= sc.out_lo[2] && x.z <= sc.out_hi[2];
+    return in;
+}
+
 template <int D, class Q>
 __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q &q) {
+    // R13: a walk outside the grown bounding box of the boundary has left the
+    // domain through a rounding gap; it ends like a capped walk (R5)
+    const bool lost = !in_bounds<D>(sc, w.x);
     // distance to the Dirichlet boundary (Q.1).  The closest point of the
     // previous step is at most dbound away (triangle inequality), which
     // prunes the search; the result is the exact closest point either way.
@@ -806,7 +843,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     }
     w.steps += 1;
     float dD = sqrtf(cl.d2);
-    if (dD < sp.epsilon || w.steps >= sp.max_steps) {
+    if (dD < sp.epsilon || w.steps >= sp.max_steps || lost) {
         // epsilon shell: g at the closest point (R5: also at the step cap)
         w.capped = !(dD < sp.epsilon);
         if (cl.rec >= 0) {

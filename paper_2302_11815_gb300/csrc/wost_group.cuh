@@ -145,7 +145,9 @@ struct GroupQ {
         if (ref_empty(T.wroot) || box_dist2<D>(T.root_lo, T.root_hi, x) >= best.d2) return best;
         uint32_t ref = T.wroot;
         int sp = 0;
+        unsigned visits = 0;
         for (;;) {
+            if (over_visit_limit(visits, T.wn_nodes, g.leader() ? gs.guard : nullptr)) break;
             if (is_leaf(ref)) {
                 uint32_t f = leaf_first(ref), c = leaf_count(ref);
                 if (g.leader()) cnt.prim_n(C_Q1, c);
@@ -196,7 +198,9 @@ struct GroupQ {
         bool found = false;
         uint32_t ref = T.wroot;
         int sp = 0;
+        unsigned visits = 0;
         for (;;) {
+            if (over_visit_limit(visits, T.wn_nodes, g.leader() ? gs.guard : nullptr)) break;
             if (is_leaf(ref)) {
                 uint32_t f = leaf_first(ref), c = leaf_count(ref);
                 if (g.leader()) cnt.prim_n(C_Q2, c);
@@ -226,6 +230,7 @@ struct GroupQ {
     // (any = true: any hit, for the visibility test of the Neumann sample)
     __device__ int ray(const TreeView &T, P3 o, P3 v, float tmax, int skip, bool any, float &t_out) {
         const int cq = any ? C_VIS : C_Q3;
+        const float tol = any ? 0.f : kEdgeTol;
         int hit_rec = -1;
         t_out = tmax;
         if (ref_empty(T.wroot)) return -1;
@@ -234,7 +239,9 @@ struct GroupQ {
         if (box_ray<D>(T.root_lo, T.root_hi, o, inv, tb) == INFINITY) return -1;
         uint32_t ref = T.wroot;
         int sp = 0;
+        unsigned visits = 0;
         for (;;) {
+            if (over_visit_limit(visits, T.wn_nodes, g.leader() ? gs.guard : nullptr)) break;
             if (is_leaf(ref)) {
                 uint32_t f = leaf_first(ref), c = leaf_count(ref);
                 if (g.leader()) cnt.prim_n(cq, c);
@@ -245,7 +252,7 @@ struct GroupQ {
                     if (k == skip) continue;
                     Prim<D> p = load_prim<D>(T.prims, (uint32_t)k);
                     float tt;
-                    if (prim_ray<D>(p, o, v, fminf(tb, t), tt)) {
+                    if (prim_ray<D>(p, o, v, fminf(tb, t), tt, tol)) {
                         t = tt;
                         rec = k;
                     }
@@ -284,7 +291,8 @@ struct GroupQ {
         if (ref_empty(T.wroot) || box_dist2<D>(T.root_lo, T.root_hi, x) > r2) return out;
         uint32_t ref = T.wroot;
         float pdf = 1.f;
-        while (!is_leaf(ref)) {
+        for (int level = 0; !is_leaf(ref); ++level) {
+            if (level > WOST_MAX_DEPTH) return out;
             if (g.leader()) cnt.node(C_Q4);
             WChild ch = load_wchild(T.wnodes, ref, g.gl);
             float w = 0.f;

@@ -81,6 +81,9 @@ struct SceneView {
     int32_t dim;
     TreeView D, N, S;
     FieldView g, h, f;
+    // the boundary's bounding box grown by its largest side on every side: a
+    // walk outside it has left the domain (through a rounding gap)
+    float out_lo[3], out_hi[3];
 };
 
 struct SolveParams {

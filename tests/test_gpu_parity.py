@@ -288,6 +288,18 @@ def test_resumable_wait_drives_the_launches(wost):
     assert a["total_steps"] == b["total_steps"] and b["launches"] >= 1
 
 
+@pytest.mark.parametrize("kernel", ["plain", "persistent", "resumable"])
+def test_walk_outside_the_grown_bounding_box_ends_at_once(wost, kernel):
+    # R13 on the GPU, against the oracle: one step, capped, g at the closest
+    # Dirichlet point; a non-finite start ends with no boundary term
+    sc = scenes.square_scene(m=4, fn="linear", params=(0.5, 1.0, 2.0, 0.0), neumann_sides=("bottom", "top"))
+    pts = np.array([[2.5, 0.25], [-1.25, 0.75], [np.nan, 0.5]], np.float32)
+    res = _gpu_solve(wost, sc, pts, 32, 3, kernel, eps=1e-3, max_steps=1024)
+    assert res["total_steps"] == 3 * 32 and res["capped_walks"] == 3 * 32
+    o = oracle.solve(oracle.Scene(sc), pts.astype(np.float64), 4, 1e-3, max_steps=1024, seed=3)
+    np.testing.assert_allclose(res["mean"], o["mean"], rtol=1e-6, atol=1e-6)
+
+
 def test_host_and_device_inputs_agree(wost):
     sc = scenes.config1(n_points=32)
     a = _gpu_solve(wost, sc, sc["points"], 64, 2, device_points=True)

@@ -400,3 +400,23 @@ def test_walk_step_invariants(which):
                             assert len(ns) == 2 and (v @ ns[0]) * (v @ ns[1]) > 0
                     checked += 1
     assert checked > 100
+
+
+def test_walk_outside_the_grown_bounding_box_ends_at_once():
+    # R13: the unit square's box grown by its side is [-1, 2]^2.  A walk
+    # started outside it ends in its first step as a capped walk with g at the
+    # closest Dirichlet point (R5); one started outside the domain but inside
+    # the grown box is not stopped by the rule; a non-finite start ends with
+    # no boundary term.
+    sc = scenes.square_scene(m=4, fn="linear", params=(0.5, 1.0, 2.0, 0.0), neumann_sides=("bottom", "top"))
+    O = oracle.Scene(sc)
+    far = np.array([[2.5, 0.25], [-1.25, 0.75]])
+    r = oracle.solve(O, far, 8, 1e-3, max_steps=1024, seed=3)
+    assert np.all(r["steps"] == 8) and np.all(r["capped"] == 8)
+    # closest Dirichlet points: (1, 0.25) on the right side, (0, 0.75) on the left
+    expect = 0.5 + 1.0 * np.array([1.0, 0.0]) + 2.0 * np.array([0.25, 0.75])
+    np.testing.assert_allclose(r["mean"], expect, rtol=0, atol=1e-12)
+    near = oracle.solve(O, np.array([[1.5, 0.5]]), 8, 1e-3, max_steps=1024, seed=3)
+    assert near["steps"][0] > 8
+    nan = oracle.solve(O, np.array([[np.nan, 0.5]]), 4, 1e-3, max_steps=1024, seed=3)
+    assert nan["steps"][0] == 4 and nan["capped"][0] == 4 and nan["mean"][0] == 0.0
