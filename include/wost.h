@@ -250,6 +250,40 @@ wost_status wost_solve_device_accumulators(wost_solve_handle *solve, const doubl
 wost_status wost_solve_work_counts(wost_solve_handle *solve, uint64_t counts[10]);
 
 /* ---------------------------------------------------------------------- */
+/* Solve without allocation.  The paper has no counterpart: this is a      */
+/* deployment variant of wost_solve.                                      */
+/* ---------------------------------------------------------------------- */
+#define WOST_STATIC_MAX_POINTS 65536
+
+/* For callers that cannot allocate device memory while they solve (a loop
+ * that must not stall on the device synchronisation of cudaMalloc/cudaFree,
+ * a process whose device memory is committed under a fixed budget).
+ * Enqueues on `stream` (NULL = the legacy default stream) the walks that
+ * wost_solve runs with WOST_KERNEL_PERSISTENT for the same arguments
+ * (n_points x walks_per_point walks of Alg. 1, walk indices first_walk..,
+ * Philox key seed) and writes the per-point mean to mean_out and, when
+ * stderr_out is not NULL, its standard error sqrt(sample variance / walks).
+ * points (device, n_points * dim floats; interior points: no Neumann
+ * normals), mean_out and stderr_out (device, n_points floats) belong to the
+ * caller and must stay valid until the stream has passed this call.
+ * The call allocates nothing: the FP64 accumulators and counters live in one
+ * fixed device array of the library (about 2 MiB, held by every device that
+ * loads the library until the process exits), which the call clears on
+ * `stream` before use.  Hence:
+ *   - n_points > WOST_STATIC_MAX_POINTS is rejected with INVALID_ARG;
+ *   - calls whose work overlaps on one device (other streams or threads)
+ *     share that array and give wrong results: order them;
+ *   - the first call on a device looks up the array's device address, which
+ *     may load the module: make it before any stream capture.
+ * If a device guard fires (traversal stack overflow or visit limit), every
+ * output is NaN.  Returns once the work is enqueued.  Errors: INVALID_ARG
+ * (null scene, points or mean_out; n_points < 1 or above the maximum;
+ * walks_per_point < 1; epsilon <= 0; r_min > epsilon; max_steps < 1), CUDA. */
+wost_status wost_solve_static(wost_scene *scene, int64_t n_points, const float *points, int32_t walks_per_point,
+                              float epsilon, float r_min, int32_t max_steps, uint64_t seed, uint32_t first_walk,
+                              float *mean_out, float *stderr_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Serving engine: continuous batching of solves with target errors.       */
 /* ---------------------------------------------------------------------- */
 /* A background scheduler owns one device stream.  Submitted requests wait

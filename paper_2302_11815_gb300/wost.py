@@ -94,6 +94,8 @@ _SIGS = {
     "wost_engine_destroy": [C.c_void_p],
     "wost_scene_autotune": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_int32,
                             C.c_void_p],
+    "wost_solve_static": [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_uint64,
+                          C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
     "wost_query_closest_dirichlet": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p],
     "wost_query_silhouette": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -471,3 +473,26 @@ def solve(scene: Scene, points, walks, epsilon, r_min=0.0, max_steps=1024, seed=
     finally:
         wost_solve_destroy(h)
     return dict(mean=mean, se=se, walks=wd, **prog)
+
+
+# ---------------------------------------------------------------------------
+# solve without allocation
+# ---------------------------------------------------------------------------
+WOST_STATIC_MAX_POINTS = 65536
+
+
+def wost_solve_static(scene, points, walks_per_point, epsilon, r_min, max_steps, seed, first_walk, mean_out,
+                      stderr_out=None, stream=None):
+    """wost_solve_static: the walks of wost_solve (persistent kernel) with no
+    allocation anywhere, for callers that cannot allocate device memory while
+    they solve.  points (n x dim), mean_out and stderr_out (n) are CUDA
+    float32 tensors owned by the caller; the call returns once the work is
+    enqueued on `stream`."""
+    for name, t in (("points", points), ("mean_out", mean_out), ("stderr_out", stderr_out)):
+        if t is not None and not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4
+                                  and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    _check(load().wost_solve_static(scene, int(points.shape[0]), points.data_ptr(), int(walks_per_point),
+                                    float(epsilon), float(r_min), int(max_steps), int(seed), int(first_walk),
+                                    mean_out.data_ptr(), None if stderr_out is None else stderr_out.data_ptr(),
+                                    _stream_ptr(stream)))
