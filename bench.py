@@ -330,6 +330,7 @@ def run_ours(args):
         mean, se, wdone, pe = wost.wost_poll(h, len(pts_h))
         wost.wost_solve_destroy(h)
         e2e_steps += pe["total_steps"]
+        steps_per_walk = pe["total_steps"] / max(1, int(wdone.sum()))
         e2e_h2d += pts_h.nbytes
         e2e_d2h += len(pts_h) * 8 * 4 + 4 * 8 + 16  # sum, sumsq, walks, steps + counters
         u = scenes.exact_u("sin2x_cos3y", (), pts_h)
@@ -377,6 +378,8 @@ def run_ours(args):
                                                  f" every resident lane runs up to {args.iters} walk steps, drawing"
                                                  f" new walks and carrying unfinished ones to the next launch",
                                          "iters_per_launch": args.iters}),
+            "points_per_s": value / (steps_per_walk * walks),
+            "mean_steps_per_walk": steps_per_walk,
             "launch_ms": per_launch_ms,
             "job_progress": {"walks_done": int(pr["walks_done"]), "steps_run": int(pr["steps_run"]),
                              "launches": int(pr["launches"])},
