@@ -26,12 +26,20 @@
 #include "wost_group.cuh"
 #include "wost_kernels.h"
 
-// Minimum resident 256-thread blocks per SM the walk kernels are compiled for
-// (bounds their registers: 1 -> no bound, 4 -> 64 registers, 5 -> 51).  A
-// build-time occupancy knob, chosen by measurement.
-#ifndef WOST_WALK_MIN_BLOCKS
-#define WOST_WALK_MIN_BLOCKS 1
+// Register caps of the walk kernels (2D and 3D instantiations).  They are
+// latency-bound (dependent node fetches, divergent traversals): more
+// resident warps beat the few spills a lower cap costs.  Measured on the
+// Koch workload (2D) with 128-thread blocks: uncapped (99 registers, 4
+// blocks/SM) 3.5e8 steps/s, 80 -> 3.9e8, 72 -> 4.1e8, 64 (8 blocks/SM) ->
+// 4.3e8, 56 (9 blocks/SM) -> 4.4e8, 48 -> 4.3e8.  Build-time knobs; 255 =
+// no cap.
+#ifndef WOST_WALK_REGS_2D
+#define WOST_WALK_REGS_2D 56
 #endif
+#ifndef WOST_WALK_REGS_3D
+#define WOST_WALK_REGS_3D 255
+#endif
+#define WOST_WALK_BOUNDS __maxnreg__(D == 2 ? WOST_WALK_REGS_2D : WOST_WALK_REGS_3D)
 
 namespace wost {
 
@@ -84,7 +92,7 @@ __device__ __forceinline__ void accumulate(const Accumulators &acc, const Walk &
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
+__global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     int warp_uniform_points) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
@@ -133,7 +141,7 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_plain(const 
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(const SceneView sc, const SolveParams sp,
+__global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_persistent(c
 // the longest walks of the solve: their steps spill into later launches
 // while the rest of the grid keeps drawing new walks.
 template <int D>
-__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_resume(const SceneView sc, const SolveParams sp,
+__global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolveParams sp,
                                                      const Accumulators acc, const ResumeState rs, int iters) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
@@ -277,7 +285,7 @@ __global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_resume(const
 // the jobs' walks; a team maps its next index to a job by binary search over
 // the jobs' first indices and runs that job's walk on that job's scene.
 template <int D>
-__global__ void __launch_bounds__(256, WOST_WALK_MIN_BLOCKS) k_walk_batch(const BatchHeader *__restrict__ hdr,
+__global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hdr,
                                                     const BatchJob *__restrict__ jobs, unsigned long long *counter,
                                                     unsigned int *guard, int stack_depth, const int *cancel) {
     const int n_jobs = hdr->n_jobs;
