@@ -31,13 +31,14 @@
 // resident warps beat the few spills a lower cap costs.  Measured on the
 // Koch workload (2D) with 128-thread blocks: uncapped (99 registers, 4
 // blocks/SM) 3.5e8 steps/s, 80 -> 3.9e8, 72 -> 4.1e8, 64 (8 blocks/SM) ->
-// 4.3e8, 56 (9 blocks/SM) -> 4.4e8, 48 -> 4.3e8.  Build-time knobs; 255 =
-// no cap.
+// 4.3e8, 56 (9 blocks/SM) -> 4.4e8, 48 -> 4.3e8; on the cube + torus
+// workload (3D): uncapped (123 registers) 5.7e7, 96 -> 6.8e7, 80 -> 7.3e7,
+// 64 -> 7.8e7.  Build-time knobs; 255 = no cap.
 #ifndef WOST_WALK_REGS_2D
 #define WOST_WALK_REGS_2D 56
 #endif
 #ifndef WOST_WALK_REGS_3D
-#define WOST_WALK_REGS_3D 255
+#define WOST_WALK_REGS_3D 64
 #endif
 #define WOST_WALK_BOUNDS __maxnreg__(D == 2 ? WOST_WALK_REGS_2D : WOST_WALK_REGS_3D)
 
