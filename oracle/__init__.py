@@ -38,7 +38,8 @@ _lib = None
 _lock = threading.Lock()
 
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
-FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6}
+FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6,
+      "exp_plane": 7}
 TRACE_COLS = ("x0", "x1", "x2", "onN", "dD", "dsil", "r", "hit", "t_boundary", "N", "S")
 
 DEFAULT_OFFSET = 1e-6      # reading R4: relative ray-origin offset on the boundary
@@ -65,7 +66,7 @@ class _Field(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("epsilon", C.c_double), ("r_min", C.c_double), ("max_steps", C.c_int),
                 ("seed", C.c_uint64), ("offset", C.c_double), ("vis_tmax", C.c_double),
-                ("n_threads", C.c_int)]
+                ("n_threads", C.c_int), ("sigma", C.c_double), ("screen_after", C.c_int)]
 
 
 def _L():
@@ -89,6 +90,15 @@ def _L():
             lib.orc_green_ball.argtypes = [C.c_int, C.c_double, C.c_double]
             lib.orc_green_ball_norm.restype = C.c_double
             lib.orc_green_ball_norm.argtypes = [C.c_int, C.c_double]
+            for nm in ("orc_bessel_i0e", "orc_bessel_i1e", "orc_bessel_k0e", "orc_bessel_k1e"):
+                getattr(lib, nm).restype = C.c_double
+                getattr(lib, nm).argtypes = [C.c_double]
+            lib.orc_screened_green_ball.restype = C.c_double
+            lib.orc_screened_green_ball.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+            lib.orc_screened_green_ball_norm.restype = C.c_double
+            lib.orc_screened_green_ball_norm.argtypes = [C.c_int, C.c_double, C.c_double]
+            lib.orc_screened_q.restype = C.c_double
+            lib.orc_screened_q.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
             lib.orc_source_radius.restype = C.c_double
             lib.orc_source_radius.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
             lib.orc_solve.restype = C.c_int
@@ -216,8 +226,10 @@ def neumann_sample(scene: Scene, x, r, seed=0, c0=0, c1=0, c2=0):
     return z[:scene.dim], nz[:scene.dim], float(pdf[0]), int(pr[0])
 
 
-def _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads):
+def _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads, sigma=0.0, screen_after=0):
     p = _Params()
+    p.sigma = float(sigma)
+    p.screen_after = int(screen_after)
     p.epsilon = float(epsilon)
     p.r_min = float(epsilon if r_min is None else r_min)
     p.max_steps = int(max_steps)
@@ -230,9 +242,12 @@ def _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads):
 
 def solve(scene: Scene, points, walks: int, epsilon: float, r_min=None, max_steps=1024, seed=0,
           normals=None, on_neumann=None, first_walk=0, offset=DEFAULT_OFFSET,
-          vis_tmax=DEFAULT_VIS_TMAX, threads=0, per_walk=False, point_base=0) -> dict:
+          vis_tmax=DEFAULT_VIS_TMAX, threads=0, per_walk=False, point_base=0, sigma=0.0,
+          screen_after=0) -> dict:
     """Runs `walks` walks from every point; returns per-point FP64 statistics.
-    Point i uses the random stream of point index point_base + i."""
+    Point i uses the random stream of point index point_base + i.  sigma > 0
+    solves the screened equation -Lap u + sigma u = f from step screen_after
+    on (App. A.2; the Tikhonov switch of Sec. 4.1)."""
     x = _d(points)
     n = len(x)
     nr = None if normals is None else _d(normals)
@@ -240,7 +255,7 @@ def solve(scene: Scene, points, walks: int, epsilon: float, r_min=None, max_step
     sm = np.zeros(n); sq = np.zeros(n)
     st = np.zeros(n, np.int64); cp = np.zeros(n, np.int64)
     pw = np.zeros(n * walks) if per_walk else None
-    p = _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads)
+    p = _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, threads, sigma, screen_after)
     used = _L().orc_solve(scene._h, n, _ptr(x), _ptr(nr), _ptr(on), int(walks), int(first_walk),
                           int(point_base), C.byref(p), _ptr(sm), _ptr(sq), _ptr(st), _ptr(cp), _ptr(pw))
     mean = sm / walks
@@ -254,13 +269,13 @@ def solve(scene: Scene, points, walks: int, epsilon: float, r_min=None, max_step
 
 def walk_trace(scene: Scene, x0, point_index=0, walk_index=0, epsilon=1e-3, r_min=None,
                max_steps=1024, seed=0, n0=None, on_neumann=False, offset=DEFAULT_OFFSET,
-               vis_tmax=DEFAULT_VIS_TMAX):
+               vis_tmax=DEFAULT_VIS_TMAX, sigma=0.0, screen_after=0):
     """One walk with its per-step trace (rows of TRACE_COLS)."""
     x = _d(x0).ravel()
     nn = None if n0 is None else _d(n0).ravel()
     rows = np.zeros((max_steps, len(TRACE_COLS)))
     val = np.zeros(1); capped = np.zeros(1, np.int32)
-    p = _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, 1)
+    p = _params(epsilon, r_min, max_steps, seed, offset, vis_tmax, 1, sigma, screen_after)
     k = _L().orc_walk_trace(scene._h, _ptr(x), _ptr(nn), int(bool(on_neumann)), int(point_index),
                             int(walk_index), C.byref(p), _ptr(rows), max_steps, _ptr(val),
                             _ptr(capped))
@@ -274,3 +289,22 @@ def exact_u(dim, fn, params, pts):
     pr[: len(params or [])] = params or []
     _L().orc_exact_u(int(dim), FN[fn], _ptr(pr), len(x), _ptr(x), _ptr(out))
     return out
+
+
+def bessel_scaled(x):
+    """(e^-x I0, e^-x I1, e^x K0, e^x K1) at each x > 0."""
+    L = _L()
+    return np.array([[L.orc_bessel_i0e(float(t)), L.orc_bessel_i1e(float(t)), L.orc_bessel_k0e(float(t)),
+                      L.orc_bessel_k1e(float(t))] for t in np.ravel(x)])
+
+
+def screened_green_ball(dim, rho, R, sigma):
+    return _L().orc_screened_green_ball(int(dim), float(rho), float(R), float(sigma))
+
+
+def screened_green_ball_norm(dim, R, sigma):
+    return _L().orc_screened_green_ball_norm(int(dim), float(R), float(sigma))
+
+
+def screened_q(dim, rho, R, sigma):
+    return _L().orc_screened_q(int(dim), float(rho), float(R), float(sigma))

@@ -46,6 +46,15 @@
  *   R7 2D source radius t = R sqrt(U1 U2); 3D t = R (1/2 + sin(asin(2U-1)/3))
  *      (inverse CDF of Beta(2,2)); both are the normalised G_B of App. A.
  *   R12 a Neumann sample at distance exactly 0 from x contributes nothing.
+ *   R14 the star radius is at most the diagonal of the boundary's bounding
+ *      box (a ball that large around any point of the box holds the whole
+ *      domain); it matters only without a Dirichlet boundary (pure Neumann
+ *      problems, Sec. 6.4), where d_D is infinite.
+ *   R15 screened steps (sigma > 0, from step screen_after on: the Tikhonov
+ *      switch of Sec. 4.1) use G^sigma_B of App. A.2 for the Neumann term,
+ *      the unscreened source density with weight |G_B| G^sigma_B / G_B for
+ *      the source term, and continue with probability Q^sigma_B(x, x_next)
+ *      drawn with the fourth uniform of slot 0 (Russian roulette).
  *   R13 a walk whose position lies outside the bounding box of the
  *      boundary grown by its largest side on every side (or is not finite)
  *      has left the domain: it ends like a capped walk (R5).  Exact
@@ -148,6 +157,73 @@ double orc_source_radius(int dim, double R, double u1, double u2) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Screened Poisson equation (App. A.2)                                */
+/* ------------------------------------------------------------------ */
+/* Exponentially scaled modified Bessel functions from their integral
+ * representations (Abramowitz & Stegun 9.6.19 and 9.6.24):
+ *   I_n(x) = (1/pi) int_0^pi e^{x cos t} cos(n t) dt,
+ *   K_n(x) = int_0^inf e^{-x cosh t} cosh(n t) dt,
+ * by the trapezoidal rule, which converges geometrically for these smooth
+ * even integrands (periodic for I, decaying double-exponentially for K). */
+#define ORC_BESSEL_N 4096
+static double bessel_ie(int n, double x) {
+    const double h = M_PI / ORC_BESSEL_N;
+    double sum = 0.0;
+    for (int j = 0; j <= ORC_BESSEL_N; ++j) {
+        double t = j * h, w = (j == 0 || j == ORC_BESSEL_N) ? 0.5 : 1.0;
+        sum += w * exp(x * (cos(t) - 1.0)) * (n ? cos(t) : 1.0);
+    }
+    return sum * h / M_PI;
+}
+static double bessel_ke(int n, double x) {
+    /* the integrand is below e^-750 beyond T */
+    const double T = acosh(1.0 + 750.0 / x);
+    const double h = T / ORC_BESSEL_N;
+    double sum = 0.0;
+    for (int j = 0; j <= ORC_BESSEL_N; ++j) {
+        double t = j * h, w = (j == 0 || j == ORC_BESSEL_N) ? 0.5 : 1.0;
+        sum += w * exp(-x * (cosh(t) - 1.0)) * (n ? cosh(t) : 1.0);
+    }
+    return sum * h;
+}
+double orc_bessel_i0e(double x) { return bessel_ie(0, x); }
+double orc_bessel_i1e(double x) { return bessel_ie(1, x); }
+double orc_bessel_k0e(double x) { return bessel_ke(0, x); }
+double orc_bessel_k1e(double x) { return bessel_ke(1, x); }
+
+/* Eq. GreensFnsScreenedPoissonBall, written with the scaled Bessel
+ * functions (2D) and exponentials (3D) so that nothing overflows. */
+double orc_screened_green_ball(int dim, double rho, double R, double sigma) {
+    const double sq = sqrt(sigma), a = R * sq, b = rho * sq;
+    if (dim == 2) {
+        double k0b = orc_bessel_k0e(b) * exp(-b);
+        double i0b_ratio = orc_bessel_i0e(b) * orc_bessel_k0e(a) / orc_bessel_i0e(a) * exp(b - 2.0 * a);
+        return (k0b - i0b_ratio) / (2.0 * M_PI);
+    }
+    /* sinh((R - rho) s) / sinh(R s) */
+    double ratio = exp(-b) * (1.0 - exp(-2.0 * (a - b))) / (1.0 - exp(-2.0 * a));
+    return ratio / (4.0 * M_PI * rho);
+}
+/* Eq. GreensFnsNormScreenedPoissonBall */
+double orc_screened_green_ball_norm(int dim, double R, double sigma) {
+    const double a = R * sqrt(sigma);
+    if (dim == 2) return (1.0 - exp(-a) / orc_bessel_i0e(a)) / sigma;
+    return (1.0 - 2.0 * a * exp(-a) / (1.0 - exp(-2.0 * a))) / sigma;
+}
+/* Eq. ScreenedPoissonKernelsSphere: Q at distance rho from the centre */
+double orc_screened_q(int dim, double rho, double R, double sigma) {
+    const double sq = sqrt(sigma), a = R * sq, b = rho * sq;
+    if (dim == 2) {
+        double k1b = orc_bessel_k1e(b) * exp(-b);
+        double i1b_ratio = orc_bessel_i1e(b) * orc_bessel_k0e(a) / orc_bessel_i0e(a) * exp(b - 2.0 * a);
+        return (k1b + i1b_ratio) * b;
+    }
+    /* (b cosh b - sinh b) e^-a / sinh a */
+    double second = ((b - 1.0) * exp(b - 2.0 * a) + (b + 1.0) * exp(-b - 2.0 * a)) / (1.0 - exp(-2.0 * a));
+    return exp(-b) * (b + 1.0) + second;
+}
+
+/* ------------------------------------------------------------------ */
 /* exact solutions used as analytic boundary data                      */
 /* ------------------------------------------------------------------ */
 static double fn_u(int dim, int fn, const double *p, V3 x) {
@@ -161,6 +237,7 @@ static double fn_u(int dim, int fn, const double *p, V3 x) {
         double rho = len(sub(x, mk(p[2], p[3], dim == 3 ? p[4] : 0.0)));
         return dim == 2 ? p[0] + p[1] * log(rho) : p[0] + p[1] / rho;
     }
+    case ORC_FN_EXP_PLANE: return p[0] * exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     default: return 0.0;
     }
 }
@@ -177,15 +254,20 @@ static V3 fn_grad(int dim, int fn, const double *p, V3 x) {
         double rho = len(d);
         return dim == 2 ? scl(d, p[1] / (rho * rho)) : scl(d, -p[1] / (rho * rho * rho));
     }
+    case ORC_FN_EXP_PLANE: {
+        double u = p[0] * exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
+        return mk(u * p[1], u * p[2], u * p[3]);
+    }
     default: return mk(0, 0, 0);
     }
 }
 /* -Laplacian(u), the source f under reading R1 */
 static double fn_neglap(int dim, int fn, const double *p, V3 x) {
-    (void)p;
     switch (fn) {
     case ORC_FN_SIN2X_COS3Y: return 13.0 * sin(2 * x.x) * cos(3 * x.y);
     case ORC_FN_BUMP: return 1.0;
+    case ORC_FN_EXP_PLANE:
+        return -(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]) * p[0] * exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     default: (void)dim; return 0.0;
     }
 }
@@ -228,6 +310,7 @@ struct orc_scene {
     orc_field g, h, f;
     double *gv, *hv, *fv;
     double blo[3], bhi[3]; /* R13: grown bounding box of the vertices */
+    double rmax;           /* R14: diagonal of the vertices' bounding box */
 };
 
 static V3 vert(const orc_scene *s, int i) { return s->V[i]; }
@@ -431,8 +514,12 @@ orc_scene *orc_scene_new(int dim, int nv, const double *vertices, int np, const 
             hi[a] = fmax(hi[a], c[a]);
         }
     }
-    double m = 0.0;
-    for (int a = 0; a < dim; ++a) m = fmax(m, hi[a] - lo[a]);
+    double m = 0.0, d2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        m = fmax(m, hi[a] - lo[a]);
+        d2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+    }
+    s->rmax = sqrt(d2);
     for (int a = 0; a < 3; ++a) {
         s->blo[a] = lo[a] - m;
         s->bhi[a] = hi[a] + m;
@@ -862,13 +949,15 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
         /* distance to the visibility silhouette (Q.2) within d_D */
         int silk;
         double dsil = q_silhouette(s, xq, dD, &silk);
-        /* star radius (R3) */
-        double r = fmin(dD, fmax(pr->r_min, dsil));
+        /* star radius (R3), at most the scene's diameter (R14) */
+        double r = fmin(fmin(dD, fmax(pr->r_min, dsil)), s->rmax);
+        /* screening coefficient of this step (Tikhonov switch, Sec. 4.1) */
+        double sig = (pr->sigma > 0 && k >= pr->screen_after) ? pr->sigma : 0.0;
         /* direction, hemisphere about -n_x on the Neumann boundary */
         uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
         uint32_t ctr[4] = {widx, pidx, (uint32_t)k, 0u}, w4[4];
         orc_philox4x32_10(ctr, key, w4);
-        double u1 = u01(w4[0]), u2 = u01(w4[1]), u3 = u01(w4[2]);
+        double u1 = u01(w4[0]), u2 = u01(w4[1]), u3 = u01(w4[2]), u4 = u01(w4[3]);
         V3 v = sample_direction(dim, u1, u2);
         if (onN && dot(nx, v) > 0) v = scl(v, -1.0);
         /* first hit with the Neumann part of the star boundary (Q.3) */
@@ -899,7 +988,8 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
                 int occluded = q_intersect_neumann(s, xq, sub(z, xq), pr->vis_tmax, zprim, &tvis, &vp);
                 if (!occluded) {
                     double alpha = onN ? 0.5 : 1.0;
-                    Nterm = orc_green_ball(dim, dz, r) * eval_h(s, zprim, z) / (alpha * pdf);
+                    double G = sig > 0 ? orc_screened_green_ball(dim, dz, r, sig) : orc_green_ball(dim, dz, r);
+                    Nterm = G * eval_h(s, zprim, z) / (alpha * pdf);
                 }
             }
         }
@@ -908,7 +998,13 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
         double ts = orc_source_radius(dim, r, dim == 2 ? u2 : u3, u3);
         if (s->f.kind != ORC_DATA_NONE) {
             double tb = len(sub(p, x));
-            if (ts < tb) Sterm = orc_green_ball_norm(dim, r) * eval_f(s, add(x, scl(v, ts)));
+            if (ts < tb) {
+                /* y drawn from G_B / |G_B|; under screening the estimate is
+                 * G^sigma_B(x,y) f(y) / pdf(y) = |G_B| (G^sigma_B / G_B)(ts) f(y) */
+                double w = orc_green_ball_norm(dim, r);
+                if (sig > 0) w *= orc_screened_green_ball(dim, ts, r, sig) / orc_green_ball(dim, ts, r);
+                Sterm = w * eval_f(s, add(x, scl(v, ts)));
+            }
         }
         /* R1: each step adds the Neumann and source terms */
         acc += Nterm + Sterm;
@@ -919,6 +1015,10 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
             row[9] = Nterm; row[10] = Sterm;
             ++*nrows;
         }
+        /* screened step (App. A.2): the walk continues to p with probability
+         * Q^sigma_B(x, p) (Russian roulette with the fourth uniform of slot 0)
+         * and is otherwise absorbed, contributing nothing more */
+        if (sig > 0 && u4 >= orc_screened_q(dim, len(sub(p, x)), r, sig)) break;
         x = p;
         nx = np;
         onN = hit;

@@ -42,8 +42,11 @@ enum { ORC_FN_ZERO = 0,        /* u = 0                                   */
        ORC_FN_QUAD3 = 3,       /* u = x^2 - y^2 + z/2                     */
        ORC_FN_BUMP = 4,        /* u = (1 - |x|^2) / (2 dim), -Lap u = 1   */
        ORC_FN_LINEAR = 5,      /* u = p0 + p1 x + p2 y + p3 z             */
-       ORC_FN_LOG_RADIAL = 6   /* 2D: p0 + p1 log|x-c|, 3D: p0 + p1/|x-c|,
+       ORC_FN_LOG_RADIAL = 6,  /* 2D: p0 + p1 log|x-c|, 3D: p0 + p1/|x-c|,
                                   c = (p2, p3, p4)                        */
+       ORC_FN_EXP_PLANE = 7    /* u = p0 exp(p1 x + p2 y + p3 z): solves the
+                                  screened equation -Lap u + sigma u = 0 for
+                                  sigma = p1^2 + p2^2 + p3^2               */
 };
 
 typedef struct {
@@ -104,6 +107,19 @@ double orc_green_ball_norm(int dim, double R);
 /* Source radius t ~ G_B(x, x + t v)/|G_B| from the uniforms of slot 0. */
 double orc_source_radius(int dim, double R, double u1, double u2);
 
+/* Exponentially scaled modified Bessel functions e^-x I0(x), e^-x I1(x),
+ * e^x K0(x), e^x K1(x), x > 0, from their integral representations. */
+double orc_bessel_i0e(double x);
+double orc_bessel_i1e(double x);
+double orc_bessel_k0e(double x);
+double orc_bessel_k1e(double x);
+/* Screened Poisson, sigma > 0 (App. A.2): Green's function of the ball
+ * B(x,R) at distance rho, its integral over the ball, and the step weight
+ * Q = P^sigma_B / P^free at distance rho <= R. */
+double orc_screened_green_ball(int dim, double rho, double R, double sigma);
+double orc_screened_green_ball_norm(int dim, double R, double sigma);
+double orc_screened_q(int dim, double rho, double R, double sigma);
+
 typedef struct {
     double epsilon, r_min;
     int max_steps;
@@ -111,6 +127,9 @@ typedef struct {
     double offset;    /* relative ray-origin offset for on-boundary points */
     double vis_tmax;  /* visibility ray end for the Neumann sample (< 1)   */
     int n_threads;    /* 0 = all cores                                     */
+    double sigma;     /* screening coefficient (0: Poisson)                */
+    int screen_after; /* steps k >= screen_after solve the screened
+                         equation (Tikhonov switch); 0 = every step        */
 } orc_params;
 
 /* Runs walks_per_point walks (walk ids first_walk ...) from each point and

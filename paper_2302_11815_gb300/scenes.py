@@ -27,7 +27,9 @@ A scene is a plain dict:
 
 Analytic solution names: zero, exp_cos (e^x cos y), sin2x_cos3y,
 quad3 (x^2 - y^2 + z/2), bump ((1-|x|^2)/(2 dim), source 1), linear
-(p0 + p1 x + p2 y + p3 z), log_radial (2D p0 + p1 log|x-c|, 3D p0 + p1/|x-c|).
+(p0 + p1 x + p2 y + p3 z), log_radial (2D p0 + p1 log|x-c|, 3D p0 + p1/|x-c|),
+exp_plane (p0 exp(p1 x + p2 y + p3 z), which solves -Lap u + sigma u = 0 for
+sigma = p1^2 + p2^2 + p3^2).
 """
 from __future__ import annotations
 
@@ -35,7 +37,7 @@ import math
 
 import numpy as np
 
-FN_NAMES = ("zero", "exp_cos", "sin2x_cos3y", "quad3", "bump", "linear", "log_radial")
+FN_NAMES = ("zero", "exp_cos", "sin2x_cos3y", "quad3", "bump", "linear", "log_radial", "exp_plane")
 
 
 # ---------------------------------------------------------------------------
@@ -66,6 +68,8 @@ def exact_u(fn: str, params, pts: np.ndarray) -> np.ndarray:
         c = np.array([p[2], p[3], p[4] if dim == 3 else 0.0])
         rho = np.sqrt((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2)
         return p[0] + p[1] * np.log(rho) if dim == 2 else p[0] + p[1] / rho
+    if fn == "exp_plane":
+        return p[0] * np.exp(p[1] * X + p[2] * Y + p[3] * Z)
     raise ValueError(fn)
 
 
@@ -96,6 +100,9 @@ def exact_grad(fn: str, params, pts: np.ndarray) -> np.ndarray:
         rho = np.linalg.norm(d, axis=1)
         s = p[1] / rho**2 if dim == 2 else -p[1] / rho**3
         g = (d[:, 0] * s, d[:, 1] * s, d[:, 2] * s)
+    elif fn == "exp_plane":
+        u = p[0] * np.exp(p[1] * X + p[2] * Y + p[3] * Z)
+        g = (u * p[1], u * p[2], u * p[3])
     else:
         raise ValueError(fn)
     return np.stack(g[:dim], 1)

@@ -420,3 +420,126 @@ def test_walk_outside_the_grown_bounding_box_ends_at_once():
     assert near["steps"][0] > 8
     nan = oracle.solve(O, np.array([[np.nan, 0.5]]), 4, 1e-3, max_steps=1024, seed=3)
     assert nan["steps"][0] == 4 and nan["capped"][0] == 4 and nan["mean"][0] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# screened Poisson equation (App. A.2) and the Tikhonov switch (Sec. 4.1)
+# ---------------------------------------------------------------------------
+def test_scaled_bessel_functions_match_scipy():
+    from scipy import special
+
+    x = np.logspace(-4, 3, 29)
+    b = oracle.bessel_scaled(x)
+    ref = np.stack([special.i0e(x), special.i1e(x), special.k0e(x), special.k1e(x)], 1)
+    np.testing.assert_allclose(b, ref, rtol=1e-10, atol=0)
+
+
+def _dG(dim, rho, R, sig, h):
+    return (oracle.screened_green_ball(dim, rho + h, R, sig) - oracle.screened_green_ball(dim, rho - h, R, sig)) / (2 * h)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("R,sig", [(0.3, 0.5), (1.5, 10.0), (0.8, 400.0)])
+def test_screened_green_function_of_the_ball(dim, R, sig):
+    G = lambda r: oracle.screened_green_ball(dim, r, R, sig)  # noqa: E731
+    sphere = 2 * math.pi if dim == 2 else 4 * math.pi
+    # zero on the sphere
+    assert abs(G(R)) < 1e-12 * abs(G(0.5 * R))
+    # -G'' - (dim-1)/r G' + sigma G = 0 away from the centre
+    for rho in (0.2 * R, 0.5 * R, 0.9 * R):
+        h = 1e-4 * rho
+        d2 = (G(rho + h) - 2 * G(rho) + G(rho - h)) / h**2
+        d1 = (G(rho + h) - G(rho - h)) / (2 * h)
+        res = -d2 - (dim - 1) / rho * d1 + sig * G(rho)
+        assert abs(res) < 1e-5 * (abs(d2) + abs(sig * G(rho))), (rho, res)
+    # unit source: the flux through a small sphere around the centre is 1
+    rho = 1e-6 * R
+    assert abs(-sphere * rho ** (dim - 1) * _dG(dim, rho, R, sig, 1e-3 * rho) - 1.0) < 1e-4
+    # Q = P^sigma_B / P^free = -|S^(dim-1)| rho^(dim-1) dG/drho at every rho
+    for rho in (0.1 * R, 0.5 * R, R):
+        q = oracle.screened_q(dim, rho, R, sig)
+        fd = -sphere * rho ** (dim - 1) * _dG(dim, rho, R, sig, 1e-5 * rho)
+        assert abs(q - fd) < 1e-6 * abs(fd), (rho, q, fd)
+        assert 0.0 <= q < 1.0
+    # |G^sigma_B| is the integral of G over the ball
+    quad, _ = integrate.quad(lambda r: G(r) * sphere * r ** (dim - 1), 0, R, limit=200, points=[1e-6 * R])
+    norm = oracle.screened_green_ball_norm(dim, R, sig)
+    assert abs(norm - quad) < 1e-8 * norm
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_screened_green_function_tends_to_the_unscreened_one(dim):
+    R, sig = 0.7, 1e-9
+    for rho in (0.05, 0.3, 0.6):
+        assert abs(oracle.screened_green_ball(dim, rho, R, sig) / oracle.green_ball(dim, rho, R) - 1) < 1e-6
+        assert abs(oracle.screened_q(dim, rho, R, sig) - 1) < 1e-6
+    # (the closed form of the norm cancels at tiny sigma: checked at 1e-6,
+    # where the true relative difference is O(R^2 sigma))
+    assert abs(oracle.screened_green_ball_norm(dim, R, 1e-6) / (R * R / (4 if dim == 2 else 6)) - 1) < 1e-5
+
+
+def _exp_plane_disk(neumann_frac, a=(1.2, -0.7)):
+    n = 128
+    mask = np.arange(n) < int(round(neumann_frac * n))
+    sc = scenes.disk_scene(n, "exp_plane", (1.0, a[0], a[1], 0.0), neumann=mask)
+    return sc, a[0] ** 2 + a[1] ** 2
+
+
+@pytest.mark.parametrize("neumann_frac", [0.0, 0.5, 1.0])
+def test_walk_screened_disk_exp_plane(neumann_frac):
+    # -Lap u + sigma u = 0 for u = exp(a.x), sigma = |a|^2: Dirichlet, mixed
+    # and pure Neumann (the screened problem is well posed without any
+    # Dirichlet boundary; walks end by Russian roulette)
+    sc, sig = _exp_plane_disk(neumann_frac)
+    rng = np.random.default_rng(5)
+    pts = scenes.ball_points(rng, 24, 2, 0.85)
+    O = oracle.Scene(sc)
+    # pure Neumann walks sum many heavy-tailed Neumann terms: more walks for
+    # a trustworthy standard error
+    walks = 2000 if neumann_frac == 1.0 else 600
+    r = oracle.solve(O, pts, walks, 1e-3, max_steps=4096, seed=17, sigma=sig)
+    u = scenes.exact_u("exp_plane", (1.0, 1.2, -0.7, 0.0), pts)
+    check_z(r["mean"] - u, r["se"], 1e-3 * 3.0, label=f"screened disk N={neumann_frac}")
+    assert r["capped"].sum() == 0
+
+
+def test_walk_screened_source_and_tikhonov_switch():
+    # u = exp(a.x) with sigma = 2|a|^2 needs f = -Lap u + sigma u = |a|^2 u,
+    # given here on a fine grid (bilinear interpolation error ~1e-5)
+    a = (0.9, 0.4)
+    sig0 = a[0] ** 2 + a[1] ** 2
+    sc = scenes.disk_scene(128, "exp_plane", (1.0, a[0], a[1], 0.0))
+    ng = 513
+    xs = np.linspace(-1.05, 1.05, ng)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    fv = sig0 * np.exp(a[0] * X + a[1] * Y)
+    sc["f"] = {"kind": "grid", "origin": [xs[0], xs[0], 0.0], "spacing": [xs[1] - xs[0]] * 2 + [1.0],
+               "dims": [ng, ng, 1], "values": fv.astype(np.float32).ravel()}
+    O = oracle.Scene(sc)
+    rng = np.random.default_rng(6)
+    pts = scenes.ball_points(rng, 16, 2, 0.8)
+    r = oracle.solve(O, pts, 800, 1e-3, max_steps=4096, seed=19, sigma=2 * sig0)
+    u = scenes.exact_u("exp_plane", (1.0, a[0], a[1], 0.0), pts)
+    check_z(r["mean"] - u, r["se"], 3e-3, label="screened source")
+    # a switch beyond every walk's length leaves the Poisson walks unchanged
+    sc0 = scenes.disk_scene(128, "exp_plane", (1.0, a[0], a[1], 0.0))
+    O0 = oracle.Scene(sc0)
+    p0 = oracle.solve(O0, pts[:8], 64, 1e-3, max_steps=4096, seed=23)
+    p1 = oracle.solve(O0, pts[:8], 64, 1e-3, max_steps=4096, seed=23, sigma=5.0, screen_after=100000)
+    np.testing.assert_array_equal(p0["mean"], p1["mean"])
+    np.testing.assert_array_equal(p0["steps"], p1["steps"])
+    # screening from step 0 shortens the walks (roulette)
+    p2 = oracle.solve(O0, pts[:8], 64, 1e-3, max_steps=4096, seed=23, sigma=50.0)
+    assert p2["steps"].sum() < p0["steps"].sum()
+
+
+def test_walk_screened_cube_exp_plane_3d():
+    a = (0.8, -0.5, 0.6)
+    sig = sum(t * t for t in a)
+    sc = scenes.cube_scene(m=4, fn="exp_plane", params=(1.0, *a), neumann_faces=(0, 3))
+    O = oracle.Scene(sc)
+    rng = np.random.default_rng(7)
+    pts = rng.uniform(-0.8, 0.8, size=(24, 3))
+    r = oracle.solve(O, pts, 1500, 1e-3, max_steps=4096, seed=29, sigma=sig)
+    u = scenes.exact_u("exp_plane", (1.0, *a), pts)
+    check_z(r["mean"] - u, r["se"], 1e-3 * 4.0, label="screened cube")
