@@ -130,9 +130,9 @@ typedef struct {
 
 /* Builds the hierarchies on the host, uploads them, returns a handle.
  * Errors: INVALID_ARG for dim not 2/3, null arrays, an index out of range, a
- * flag > 1, non-finite coordinates, a field whose values are missing, no
- * Dirichlet primitive (pure Neumann problems need the regularisation of
- * Sec. 6.4, which this library does not provide); OUT_OF_MEMORY; CUDA. */
+ * flag > 1, non-finite coordinates, a field whose values are missing;
+ * OUT_OF_MEMORY; CUDA.  A scene without Dirichlet primitives (a pure
+ * Neumann problem, Sec. 6.4) is accepted; its solves need sigma > 0. */
 wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out);
 wost_status wost_scene_destroy(wost_scene *scene);
 wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out);
@@ -174,6 +174,15 @@ typedef struct {
     int32_t kernel;            /* wost_kernel                                  */
     int32_t block_size;        /* threads per block, 0 = tuned default         */
     void *stream;              /* cudaStream_t to run on, NULL = library stream */
+    float sigma;               /* screening coefficient >= 0 of the screened
+                                  Poisson equation -Lap u + sigma u = f
+                                  (Sec. 2, App. A.2); 0 = Poisson            */
+    int32_t screen_after;      /* steps k >= screen_after solve the screened
+                                  equation, earlier ones the Poisson equation:
+                                  the Tikhonov switch of Sec. 4.1 for pure
+                                  Neumann problems (0 = every step).  Screened
+                                  steps end walks by Russian roulette with
+                                  the step weight Q of App. A.2              */
 } wost_solve_desc;
 
 typedef struct {
@@ -193,7 +202,8 @@ typedef struct {
 /* Starts a solve asynchronously on the stream and returns its handle.
  * The caller's arrays are copied before return.  Errors: INVALID_ARG
  * (n_points < 1, walks < 1, epsilon <= 0, r_min > epsilon, max_steps < 1,
- * a null points array), OUT_OF_MEMORY, CUDA. */
+ * a null points array, sigma < 0 or not finite, screen_after < 0, sigma = 0
+ * on a scene without Dirichlet primitives), OUT_OF_MEMORY, CUDA. */
 wost_status wost_solve(wost_scene *scene, const wost_solve_desc *desc, wost_solve_handle **out);
 
 /* Resumable solves (desc->kernel = WOST_KERNEL_RESUMABLE): wost_solve
@@ -248,6 +258,17 @@ wost_status wost_solve_device_accumulators(wost_solve_handle *solve, const doubl
  * Neumann sample; counts[5..9] the primitive tests of the same queries.
  * INVALID_ARG for a solve started with another kernel. */
 wost_status wost_solve_work_counts(wost_solve_handle *solve, uint64_t counts[10]);
+
+/* The screened-equation functions the walks evaluate (App. A.2): at each
+ * of n pairs, G[i] = G^sigma_B(rho[i]) of the ball of radius R[i] (Eq.
+ * GreensFnsScreenedPoissonBall) and Q[i] = Q^sigma_B(rho[i]) (Eq.
+ * ScreenedPoissonKernelsSphere), 0 < rho[i] <= R[i].  All arrays are device
+ * float arrays of the current device (G or Q may be NULL); single precision,
+ * the Bessel functions by the approximations of Abramowitz & Stegun 9.8.
+ * Enqueued on `stream`.  Errors: INVALID_ARG (dim, sigma <= 0, null rho or
+ * R), CUDA. */
+wost_status wost_screened_kernels(int32_t dim, int64_t n, const float *rho, const float *R, float sigma, float *G,
+                                  float *Q, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Solve without allocation.  The paper has no counterpart: this is a      */

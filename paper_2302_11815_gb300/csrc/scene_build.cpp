@@ -447,7 +447,6 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
         }
         (d.flags[p] ? Nl : Dl).push_back(p);
     }
-    if (Dl.empty()) return "no Dirichlet primitive (pure Neumann problems are not supported)";
 
     // scene bounds
     for (int a = 0; a < 3; ++a) {

@@ -107,10 +107,13 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         {
             float m = 0.f;
             for (int a = 0; a < H.dim; ++a) m = std::max(m, H.hi[a] - H.lo[a]);
+            float d2 = 0.f;
             for (int a = 0; a < 3; ++a) {
                 s->view.out_lo[a] = H.lo[a] - m;
                 s->view.out_hi[a] = H.hi[a] + m;
+                if (a < H.dim) d2 += (H.hi[a] - H.lo[a]) * (H.hi[a] - H.lo[a]);
             }
+            s->view.rmax = std::sqrt(d2);
         }
 #if WOST_TEAM == 1
         // binary trees: one pending subtree per level
@@ -185,6 +188,11 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     float rmin = d->r_min == 0 ? d->epsilon : d->r_min;
     if (!(rmin > 0) || rmin > d->epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
     if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (!(d->sigma >= 0) || !std::isfinite(d->sigma)) return fail(WOST_ERR_INVALID_ARG, "sigma must be >= 0");
+    if (d->screen_after < 0) return fail(WOST_ERR_INVALID_ARG, "screen_after must be >= 0");
+    if (scene->host.n_dirichlet == 0 && !(d->sigma > 0))
+        return fail(WOST_ERR_INVALID_ARG, "a scene without Dirichlet primitives needs sigma > 0 (Tikhonov "
+                                          "regularisation of the pure Neumann problem)");
     if (d->memory != WOST_MEM_HOST && d->memory != WOST_MEM_DEVICE)
         return fail(WOST_ERR_INVALID_ARG, "memory must be HOST or DEVICE");
     if (d->kernel != WOST_KERNEL_PLAIN && d->kernel != WOST_KERNEL_PERSISTENT && d->kernel != WOST_KERNEL_COUNTING &&
@@ -245,6 +253,9 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     sp.offset = 1e-6f;
     sp.vis_tmax = 1.f - 1e-4f;
     sp.stack_depth = scene->stack_depth;
+    sp.sigma = d->sigma;
+    sp.sqrt_sigma = std::sqrt(d->sigma);
+    sp.screen_after = d->screen_after;
     Accumulators &acc = h->acc;
     acc = Accumulators{};
     acc.sum = (double *)h->sum.p;
@@ -617,6 +628,15 @@ wost_status wost_solve_work_counts(wost_solve_handle *h, uint64_t counts[10]) {
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     CK(cudaEventSynchronize(h->ev_done), "solve");
     CK(cudaMemcpy(counts, h->counts.p, 10 * 8, cudaMemcpyDeviceToHost), "copy counts");
+    return WOST_OK;
+}
+
+extern "C" wost_status wost_screened_kernels(int32_t dim, int64_t n, const float *rho, const float *R, float sigma,
+                                             float *G, float *Q, void *stream) {
+    if (dim != 2 && dim != 3) return fail(WOST_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (n < 0 || (n > 0 && (!rho || !R))) return fail(WOST_ERR_INVALID_ARG, "null argument or negative count");
+    if (!(sigma > 0) || !std::isfinite(sigma)) return fail(WOST_ERR_INVALID_ARG, "sigma must be > 0");
+    CK(launch_screened_kernels(dim, n, rho, R, sigma, G, Q, (cudaStream_t)stream), "kernel launch");
     return WOST_OK;
 }
 

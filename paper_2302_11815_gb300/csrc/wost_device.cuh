@@ -18,7 +18,11 @@
 //   R6 Q.4 child weight 1/d to the child box centre (the 1/(4 pi) of the
 //      free-space Green's function cancels in the child probabilities);
 //   R7 2D source radius R sqrt(U1 U2), 3D R (1/2 + sin(asin(2U-1)/3));
-//   R12 a Neumann sample at distance 0 from x contributes nothing.
+//   R12 a Neumann sample at distance 0 from x contributes nothing;
+//   R13 a walk outside the grown bounding box ends like a capped walk;
+//   R14 the star radius is at most the scene's diameter;
+//   R15 screened steps (App. A.2): G^sigma_B for the Neumann term, the
+//       unscreened source sample reweighted, Russian roulette with Q.
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11); key = seed, counter
 // = (walk, point, step, slot); slot 0 drives direction and source, slots
 // 1, 2, ... the Neumann sampler.
@@ -715,6 +719,7 @@ __device__ __noinline__ float fn_u(int fn, const float *p, P3 x) {
         float rho = sqrtf(dotp<D>(d, d));
         return D == 2 ? p[0] + p[1] * logf(rho) : p[0] + p[1] / rho;
     }
+    case 7: return p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     default: return 0.f;
     }
 }
@@ -734,14 +739,113 @@ __device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
         float rho2 = dotp<D>(d, d);
         return D == 2 ? d * (p[1] / rho2) : d * (-p[1] / (rho2 * sqrtf(rho2)));
     }
+    case 7: {
+        float u = p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
+        return mk(u * p[1], u * p[2], u * p[3]);
+    }
     default: return mk(0.f, 0.f, 0.f);
     }
 }
 template <int D>
-__device__ __noinline__ float fn_neglap(int fn, P3 x) {
+__device__ __noinline__ float fn_neglap(int fn, const float *p, P3 x) {
     if (fn == 2) return 13.f * sinf(2.f * x.x) * cosf(3.f * x.y);
     if (fn == 4) return 1.f;
+    if (fn == 7) return -(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]) * p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     return 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// screened Poisson equation (App. A.2)
+// ---------------------------------------------------------------------------
+// Exponentially scaled modified Bessel functions e^-x I0, e^-x I1, e^x K0,
+// e^x K1 (x > 0) by the polynomial approximations of Abramowitz & Stegun,
+// Handbook of Mathematical Functions, 9.8.1-9.8.8 (absolute/relative error
+// below 2.2e-7 in the scaled forms).
+__device__ __forceinline__ float poly(float t, const float *c, int n) {
+    float r = c[n - 1];
+    for (int i = n - 2; i >= 0; --i) r = fmaf(r, t, c[i]);
+    return r;
+}
+__device__ __noinline__ float bessel_i0e(float x) {
+    if (x <= 3.75f) {
+        const float c[7] = {1.f, 3.5156229f, 3.0899424f, 1.2067492f, 0.2659732f, 0.0360768f, 0.0045813f};
+        float t = x * (1.f / 3.75f);
+        return poly(t * t, c, 7) * expf(-x);
+    }
+    const float c[9] = {0.39894228f, 0.01328592f, 0.00225319f, -0.00157565f, 0.00916281f,
+                        -0.02057706f, 0.02635537f, -0.01647633f, 0.00392377f};
+    return poly(3.75f / x, c, 9) * rsqrtf(x);
+}
+__device__ __noinline__ float bessel_i1e(float x) {
+    if (x <= 3.75f) {
+        const float c[7] = {0.5f, 0.87890594f, 0.51498869f, 0.15084934f, 0.02658733f, 0.00301532f, 0.00032411f};
+        float t = x * (1.f / 3.75f);
+        return x * poly(t * t, c, 7) * expf(-x);
+    }
+    const float c[9] = {0.39894228f, -0.03988024f, -0.00362018f, 0.00163801f, -0.01031555f,
+                        0.02282967f, -0.02895312f, 0.01787654f, -0.00420059f};
+    return poly(3.75f / x, c, 9) * rsqrtf(x);
+}
+__device__ __noinline__ float bessel_k0e(float x) {
+    if (x <= 2.f) {
+        const float c[7] = {-0.57721566f, 0.42278420f, 0.23069756f, 0.03488590f, 0.00262698f, 0.00010750f,
+                            0.00000740f};
+        float h = 0.5f * x;
+        return (-logf(h) * bessel_i0e(x) * expf(x) + poly(h * h, c, 7)) * expf(x);
+    }
+    const float c[7] = {1.25331414f, -0.07832358f, 0.02189568f, -0.01062446f, 0.00587872f, -0.00251540f,
+                        0.00053208f};
+    return poly(2.f / x, c, 7) * rsqrtf(x);
+}
+__device__ __noinline__ float bessel_k1e(float x) {
+    if (x <= 2.f) {
+        const float c[7] = {1.f, 0.15443144f, -0.67278579f, -0.18156897f, -0.01919402f, -0.00110404f,
+                            -0.00004686f};
+        float h = 0.5f * x;
+        return (x * logf(h) * bessel_i1e(x) * expf(x) + poly(h * h, c, 7)) / x * expf(x);
+    }
+    const float c[7] = {1.25331414f, 0.23498619f, -0.03655620f, 0.01504268f, -0.00780353f, 0.00325614f,
+                        -0.00068245f};
+    return poly(2.f / x, c, 7) * rsqrtf(x);
+}
+
+// Green's function of the ball B(x,R) at distance rho (Eq.
+// GreensFnsScreenedPoissonBall), sqs = sqrt(sigma); written with the scaled
+// Bessel functions and exponentials so that nothing overflows.
+template <int D>
+__device__ __noinline__ float screened_green(float rho, float R, float sqs) {
+    const float a = R * sqs, b = rho * sqs;
+    if constexpr (D == 2) {
+        float k0b = bessel_k0e(b) * expf(-b);
+        float ratio = bessel_i0e(b) * bessel_k0e(a) / bessel_i0e(a) * expf(b - 2.f * a);
+        return (k0b - ratio) * (0.5f / 3.14159265358979f);
+    } else {
+        // sinh((R - rho) s) / sinh(R s)
+        float ratio = expf(-b) * expm1f(-2.f * (a - b)) / expm1f(-2.f * a);
+        return ratio / (4.f * 3.14159265358979f * rho);
+    }
+}
+// step weight Q^sigma_B at distance rho <= R (Eq. ScreenedPoissonKernelsSphere)
+template <int D>
+__device__ __noinline__ float screened_q(float rho, float R, float sqs) {
+    const float a = R * sqs, b = rho * sqs;
+    if constexpr (D == 2) {
+        float k1b = bessel_k1e(b) * expf(-b);
+        float ratio = bessel_i1e(b) * bessel_k0e(a) / bessel_i0e(a) * expf(b - 2.f * a);
+        return (k1b + ratio) * b;
+    } else {
+        // (b cosh b - sinh b) e^-a / sinh a; its series b^3/3 (1 + b^2/10 +
+        // b^4/280) for small b, where the exponentials cancel
+        float denom = -expm1f(-2.f * a);
+        float second;
+        if (b < 0.1f) {
+            float b2 = b * b;
+            second = (b2 * b * (1.f / 3.f)) * (1.f + b2 * (0.1f + b2 * (1.f / 280.f))) * 2.f * expf(-2.f * a) / denom;
+        } else {
+            second = ((b - 1.f) * expf(b - 2.f * a) + (b + 1.f) * expf(-b - 2.f * a)) / denom;
+        }
+        return expf(-b) * (b + 1.f) + second;
+    }
 }
 
 template <int D>
@@ -826,7 +930,9 @@ __device__ __forceinline__ bool in_bounds(const SceneView &sc, P3 x) {
     return in;
 }
 
-template <int D, class Q>
+// SCR: compiled with the screened-equation terms (R15); the Poisson-only
+// instantiation keeps them, and their registers, out of the hot loop.
+template <int D, bool SCR, class Q>
 __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q &q) {
     // R13: a walk outside the grown bounding box of the boundary has left the
     // domain through a rounding gap; it ends like a capped walk (R5)
@@ -858,7 +964,11 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     P3 xq = w.onN ? w.x - w.n * delta : w.x;
     // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
     float dsil = q.silhouette(sc.S, xq, dD);
-    float r = fminf(dD, fmaxf(sp.r_min, dsil));
+    // (R14: at most the scene's diameter, which matters without Dirichlet data)
+    float r = fminf(fminf(dD, fmaxf(sp.r_min, dsil)), sc.rmax);
+    // screening of this step (R15: from step screen_after on)
+    float sqs = 0.f;
+    if constexpr (SCR) sqs = (sp.sigma > 0.f && w.steps - 1 >= sp.screen_after) ? sp.sqrt_sigma : 0.f;
     // direction: uniform, flipped into the hemisphere about -n_x on the boundary
     uint32_t k = (uint32_t)(w.steps - 1);
     uint4 rb = philox10(make_uint4(w.index, w.point, k, 0u), sp.key0, sp.key1);
@@ -910,6 +1020,9 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
                     }
                     float G = D == 2 ? logf(r / dzl) * (0.5f / 3.14159265358979f)
                                      : (1.f / dzl - 1.f / r) * (0.25f / 3.14159265358979f);
+                    if constexpr (SCR) {
+                        if (sqs > 0.f) G = screened_green<D>(dzl, r, sqs);
+                    }
                     float alpha = w.onN ? 0.5f : 1.f;
                     Nterm = G * hv / (alpha * zs.pdf);
                 }
@@ -928,14 +1041,28 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
         P3 pd = p - w.x;
         if (ts * ts < dotp<D>(pd, pd)) {
             P3 y = w.x + v * ts;
-            float fv = sc.f.kind == FIELD_ANALYTIC ? fn_neglap<D>(sc.f.fn, y) : grid_eval<D>(sc.f, y);
-            Sterm = (D == 2 ? 0.25f : (1.f / 6.f)) * r * r * fv;
+            float fv = sc.f.kind == FIELD_ANALYTIC ? fn_neglap<D>(sc.f.fn, sc.f.params, y) : grid_eval<D>(sc.f, y);
+            float wS = (D == 2 ? 0.25f : (1.f / 6.f)) * r * r;
+            if constexpr (SCR) {
+                if (sqs > 0.f) {  // R15: the unscreened sample reweighted by G^sigma_B / G_B
+                    float G0 = D == 2 ? logf(r / ts) * (0.5f / 3.14159265358979f)
+                                      : (1.f / ts - 1.f / r) * (0.25f / 3.14159265358979f);
+                    wS *= screened_green<D>(ts, r, sqs) / G0;
+                }
+            }
+            Sterm = wS * fv;
         }
     }
     // R1: the step adds the Neumann and source terms
     w.acc += Nterm + Sterm;
     P3 mv = p - w.x;
-    w.dbound = dD + sqrtf(dotp<D>(mv, mv));
+    float moved = sqrtf(dotp<D>(mv, mv));
+    // R15: a screened walk goes on to p with probability Q^sigma_B(x, p)
+    // (Russian roulette on the fourth uniform of slot 0), else it ends here
+    if constexpr (SCR) {
+        if (sqs > 0.f && u01(rb.w) >= screened_q<D>(moved, r, sqs)) return true;
+    }
+    w.dbound = dD + moved;
     w.x = p;
     w.n = np;
     w.onN = hrec >= 0;

@@ -84,6 +84,7 @@ struct SceneView {
     // the boundary's bounding box grown by its largest side on every side: a
     // walk outside it has left the domain (through a rounding gap)
     float out_lo[3], out_hi[3];
+    float rmax;  // diagonal of the boundary's bounding box: bound on the star radius
 };
 
 struct SolveParams {
@@ -100,6 +101,9 @@ struct SolveParams {
     float offset;               // relative ray-origin offset on the boundary
     float vis_tmax;             // visibility ray end for the Neumann sample
     int32_t stack_depth;        // shared-memory stack entries per walk (thread or team)
+    float sigma;                // screening coefficient (0: Poisson)
+    float sqrt_sigma;
+    int32_t screen_after;       // steps k >= screen_after are screened (Tikhonov switch)
 };
 
 struct Accumulators {

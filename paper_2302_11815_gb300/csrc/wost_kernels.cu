@@ -92,7 +92,7 @@ __device__ __forceinline__ void accumulate(const Accumulators &acc, const Walk &
     if (w.capped) atomicAdd(acc.capped, 1ull);
 }
 
-template <int D>
+template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     int warp_uniform_points) {
     Cnt<false> cnt;
@@ -110,7 +110,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolvePar
     // the warp reconverges after every step (see k_walk_persistent)
     bool done = !active;
     while (__any_sync(0xffffffffu, !done)) {
-        if (!done) done = walk_step<D>(sc, sp, w, q);
+        if (!done) done = walk_step<D, SCR>(sc, sp, w, q);
         __syncwarp();
     }
     const bool own = active && g.leader();  // one lane reports each walk
@@ -141,7 +141,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolvePar
     }
 }
 
-template <int D>
+template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
     Cnt<false> cnt;
@@ -182,7 +182,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const Sol
         }
         if (!__any_sync(FULL, have)) break;
         if (have) {
-            if (walk_step<D>(sc, sp, w, q)) {
+            if (walk_step<D, SCR>(sc, sp, w, q)) {
                 if (g.leader()) accumulate(acc, w);
                 have = false;
             }
@@ -197,7 +197,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const Sol
 // is a sequence of such launches over a fixed grid, so no launch waits for
 // the longest walks of the solve: their steps spill into later launches
 // while the rest of the grid keeps drawing new walks.
-template <int D>
+template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolveParams sp,
                                                      const Accumulators acc, const ResumeState rs, int iters) {
     Cnt<false> cnt;
@@ -252,7 +252,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolvePa
         if (!__any_sync(FULL, have)) break;
         if (have) {
             ++ran;
-            if (walk_step<D>(sc, sp, w, q)) {
+            if (walk_step<D, SCR>(sc, sp, w, q)) {
                 if (g.leader()) accumulate(acc, w);
                 have = false;
             }
@@ -338,7 +338,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hd
         }
         if (!__any_sync(FULL, job >= 0 || !drained)) break;
         if (job >= 0) {
-            if (walk_step<D>(*jobs[job].scene, jobs[job].sp, w, q)) {
+            if (walk_step<D, true>(*jobs[job].scene, jobs[job].sp, w, q)) {
                 if (g.leader()) accumulate(jobs[job].acc, w);
                 job = -1;
             }
@@ -400,7 +400,7 @@ cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_po
 
 // Counting variant of the plain kernel: same walks, plus per-query node
 // visits and primitive tests summed into stats[2 * C_NQ] (nodes then prims).
-template <int D>
+template <int D, bool SCR>
 __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     unsigned long long *stats) {
     Cnt<true> cnt;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const So
     int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
     uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
     walk_init<D>(sp, w, pt, j);
-    while (!walk_step<D>(sc, sp, w, q)) {
+    while (!walk_step<D, SCR>(sc, sp, w, q)) {
     }
     if (!g.leader()) return;
     accumulate(acc, w);
@@ -489,19 +489,38 @@ __global__ void k_query_sample(const SceneView sc, int64_t n, const float *pts, 
     prim[i] = s.rec >= 0 ? __ldg(sc.N.ids + s.rec) : -1;
 }
 
+// Eqs. GreensFnsScreenedPoissonBall and ScreenedPoissonKernelsSphere at n
+// (rho, R) pairs: the functions the screened walks evaluate (App. A.2)
+template <int D>
+__global__ void k_screened_kernels(int64_t n, const float *rho, const float *R, float sqs, float *G, float *Q) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float r = rho[i], RR = R[i];
+    if (G) G[i] = screened_green<D>(r, RR, sqs);
+    if (Q) Q[i] = screened_q<D>(r, RR, sqs);
+}
+
 // ------------------------------- launchers --------------------------------
 static size_t smem_bytes(int depth, int block) { return (size_t)depth * (block / WOST_TEAM) * sizeof(int2); }
 
-template <int D>
-static cudaError_t set_smem_attrs(size_t bytes) {
-    cudaError_t e = cudaSuccess;
-    if (bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_walk_plain<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_walk_persistent<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    }
-    return e;
+// sets the dynamic shared-memory limit of kernel k when above the default
+static cudaError_t smem_limit(const void *k, size_t bytes) {
+    return bytes > 48 * 1024 ? cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+                             : cudaSuccess;
 }
+
+// The walk kernels come in a Poisson-only and a screened instantiation
+// (SCR); a solve with sigma > 0 runs the screened one.
+#define WOST_DISPATCH(dim, scr, ...)                                  \
+    do {                                                              \
+        if ((dim) == 2) {                                             \
+            if (scr) { constexpr int D_ = 2; constexpr bool S_ = true; __VA_ARGS__; }   \
+            else { constexpr int D_ = 2; constexpr bool S_ = false; __VA_ARGS__; }      \
+        } else {                                                      \
+            if (scr) { constexpr int D_ = 3; constexpr bool S_ = true; __VA_ARGS__; }   \
+            else { constexpr int D_ = 3; constexpr bool S_ = false; __VA_ARGS__; }      \
+        }                                                             \
+    } while (0)
 
 cudaError_t launch_walk_plain(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
                               cudaStream_t s) {
@@ -510,13 +529,12 @@ cudaError_t launch_walk_plain(const SceneView &sc, const SolveParams &sp, const 
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
     int uniform = (sp.walks_per_point % (32 / WOST_TEAM) == 0) && (block % 32 == 0);
-    cudaError_t e = sc.dim == 2 ? set_smem_attrs<2>(sm) : set_smem_attrs<3>(sm);
-    if (e != cudaSuccess) return e;
-    if (sc.dim == 2)
-        k_walk_plain<2><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, uniform);
-    else
-        k_walk_plain<3><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, uniform);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    WOST_DISPATCH(sc.dim, sp.sigma > 0.f, {
+        e = smem_limit((const void *)k_walk_plain<D_, S_>, sm);
+        if (e == cudaSuccess) k_walk_plain<D_, S_><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, uniform);
+    });
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
@@ -525,16 +543,12 @@ cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const 
     uint64_t grid = (total * WOST_TEAM + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
-    if (sm > 48 * 1024) {
-        cudaError_t e = sc.dim == 2 ? cudaFuncSetAttribute(k_walk_count<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                                    : cudaFuncSetAttribute(k_walk_count<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    if (sc.dim == 2)
-        k_walk_count<2><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, stats);
-    else
-        k_walk_count<3><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, stats);
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    WOST_DISPATCH(sc.dim, sp.sigma > 0.f, {
+        e = smem_limit((const void *)k_walk_count<D_, S_>, sm);
+        if (e == cudaSuccess) k_walk_count<D_, S_><<<(unsigned)grid, block, sm, s>>>(sc, sp, acc, stats);
+    });
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
@@ -564,44 +578,53 @@ cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *j
     return cudaGetLastError();
 }
 
-cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out) {
-    int dev = 0, sms = 0, per_sm = 0;
+// resident blocks per SM of both instantiations of a walk kernel (the
+// smaller count), with their shared-memory limits set
+template <template <int, bool> class K>
+static cudaError_t walk_grid(int dim, int block, int depth, int *blocks_out) {
+    int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     size_t sm = smem_bytes(depth, block);
-    if (e == cudaSuccess) e = dim == 2 ? set_smem_attrs<2>(sm) : set_smem_attrs<3>(sm);
-    if (e == cudaSuccess)
-        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<2>, block, sm)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_persistent<3>, block, sm);
+    int per[2] = {0, 0};
+    for (int scr = 0; scr < 2 && e == cudaSuccess; ++scr) {
+        const void *k = K<2, false>::get(dim, scr != 0);
+        e = smem_limit(k, sm);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[scr], k, block, sm);
+    }
     if (e != cudaSuccess) return e;
-    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
+    int p = per[0] < per[1] ? per[0] : per[1];
+    *blocks_out = sms * (p > 0 ? p : 1);
     return cudaSuccess;
+}
+template <int, bool>
+struct PersistentK {
+    static const void *get(int dim, bool scr) {
+        return dim == 2 ? (scr ? (const void *)k_walk_persistent<2, true> : (const void *)k_walk_persistent<2, false>)
+                        : (scr ? (const void *)k_walk_persistent<3, true> : (const void *)k_walk_persistent<3, false>);
+    }
+};
+template <int, bool>
+struct ResumeK {
+    static const void *get(int dim, bool scr) {
+        return dim == 2 ? (scr ? (const void *)k_walk_resume<2, true> : (const void *)k_walk_resume<2, false>)
+                        : (scr ? (const void *)k_walk_resume<3, true> : (const void *)k_walk_resume<3, false>);
+    }
+};
+
+cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out) {
+    return walk_grid<PersistentK>(dim, block, depth, blocks_out);
 }
 
 cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
                                    int blocks, cudaStream_t s) {
     size_t sm = smem_bytes(sp.stack_depth, block);
-    if (sc.dim == 2)
-        k_walk_persistent<2><<<blocks, block, sm, s>>>(sc, sp, acc);
-    else
-        k_walk_persistent<3><<<blocks, block, sm, s>>>(sc, sp, acc);
+    WOST_DISPATCH(sc.dim, sp.sigma > 0.f, (k_walk_persistent<D_, S_><<<blocks, block, sm, s>>>(sc, sp, acc)));
     return cudaGetLastError();
 }
 
 cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t sm = smem_bytes(depth, block);
-    if (e == cudaSuccess && sm > 48 * 1024)
-        e = dim == 2 ? cudaFuncSetAttribute(k_walk_resume<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                     : cudaFuncSetAttribute(k_walk_resume<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_resume<2>, block, sm)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_resume<3>, block, sm);
-    if (e != cudaSuccess) return e;
-    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
-    return cudaSuccess;
+    return walk_grid<ResumeK>(dim, block, depth, blocks_out);
 }
 
 int64_t resume_slots(int block, int blocks) { return (int64_t)blocks * (block / WOST_TEAM); }
@@ -609,10 +632,7 @@ int64_t resume_slots(int block, int blocks) { return (int64_t)blocks * (block / 
 cudaError_t launch_walk_resume(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
     size_t sm = smem_bytes(sp.stack_depth, block);
-    if (sc.dim == 2)
-        k_walk_resume<2><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
-    else
-        k_walk_resume<3><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
+    WOST_DISPATCH(sc.dim, sp.sigma > 0.f, (k_walk_resume<D_, S_><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters)));
     return cudaGetLastError();
 }
 
@@ -682,6 +702,19 @@ cudaError_t launch_query_sample(const SceneView &sc, int64_t n, const float *pts
         k_query_sample<2><<<grid, block, 0, s>>>(sc, n, pts, r, k0, k1, c1, c2, z, pdf, prim);
     else
         k_query_sample<3><<<grid, block, 0, s>>>(sc, n, pts, r, k0, k1, c1, c2, z, pdf, prim);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_screened_kernels(int dim, int64_t n, const float *rho, const float *R, float sigma, float *G,
+                                    float *Q, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    unsigned grid = (unsigned)((n + block - 1) / block);
+    float sqs = sqrtf(sigma);
+    if (dim == 2)
+        k_screened_kernels<2><<<grid, block, 0, s>>>(n, rho, R, sqs, G, Q);
+    else
+        k_screened_kernels<3><<<grid, block, 0, s>>>(n, rho, R, sqs, G, Q);
     return cudaGetLastError();
 }
 

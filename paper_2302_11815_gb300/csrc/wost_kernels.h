@@ -26,6 +26,8 @@ cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out);
 int64_t resume_slots(int block, int blocks);
 cudaError_t launch_walk_resume(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s);
+cudaError_t launch_screened_kernels(int dim, int64_t n, const float *rho, const float *R, float sigma, float *G,
+                                    float *Q, cudaStream_t s);
 cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pts, float *dist, float *closest,
                                  int32_t *prim, int depth, unsigned int *guard, cudaStream_t s);
 cudaError_t launch_query_silhouette(const SceneView &sc, int64_t n, const float *pts, const float *rmax, float *dist,

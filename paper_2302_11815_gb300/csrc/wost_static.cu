@@ -86,6 +86,8 @@ extern "C" wost_status wost_solve_static(wost_scene *scene, int64_t n_points, co
     const float rmin = r_min == 0 ? epsilon : r_min;
     if (!(rmin > 0) || rmin > epsilon) return fail(WOST_ERR_INVALID_ARG, "need 0 < r_min <= epsilon");
     if (max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
+    if (scene->host.n_dirichlet == 0)
+        return fail(WOST_ERR_INVALID_ARG, "a scene without Dirichlet primitives needs sigma > 0: use wost_solve");
     cudaStream_t stream = (cudaStream_t)stream_arg;
     CK(cudaSetDevice(scene->device), "cudaSetDevice");
     unsigned char *s = nullptr;

@@ -66,7 +66,7 @@ class wost_solve_desc(C.Structure):
                 ("on_neumann", C.c_void_p), ("memory", C.c_int32), ("walks_per_point", C.c_int32),
                 ("epsilon", C.c_float), ("r_min", C.c_float), ("max_steps", C.c_int32), ("seed", C.c_uint64),
                 ("first_walk", C.c_uint32), ("kernel", C.c_int32), ("block_size", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("sigma", C.c_float), ("screen_after", C.c_int32)]
 
 
 class wost_progress(C.Structure):
@@ -94,6 +94,8 @@ _SIGS = {
     "wost_engine_destroy": [C.c_void_p],
     "wost_scene_autotune": [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_float, C.c_int32,
                             C.c_void_p],
+    "wost_screened_kernels": [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                              C.c_void_p],
     "wost_solve_static": [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_uint64,
                           C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
     "wost_query_closest_dirichlet": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -228,13 +230,15 @@ def wost_scene_get_info(h) -> dict:
 
 
 def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
-               kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None):
+               kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
+               screen_after=0):
     """Starts a solve.  `points` is a numpy array (host) or a torch CUDA
-    tensor (device); normals/on_neumann likewise.  Returns the handle."""
+    tensor (device); normals/on_neumann likewise.  sigma > 0 solves the
+    screened equation from step screen_after on.  Returns the handle."""
     lib = load()
     keep = []
     d = _solve_desc(keep, points, walks_per_point, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                    normals, on_neumann, stream)
+                    normals, on_neumann, stream, sigma, screen_after)
     h = C.c_void_p()
     _check(lib.wost_solve(scene, C.byref(d), C.byref(h)))
     return h
@@ -317,8 +321,11 @@ def wost_engine_destroy(engine):
 
 
 def _solve_desc(keep, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
-                kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None):
+                kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
+                screen_after=0):
     d = wost_solve_desc()
+    d.sigma = float(sigma)
+    d.screen_after = int(screen_after)
     if isinstance(points, np.ndarray):
         pts = np.ascontiguousarray(points, np.float32)
         keep.append(pts)
@@ -461,10 +468,10 @@ class Scene:
 
 
 def solve(scene: Scene, points, walks, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0, kernel="plain",
-          block_size=0, normals=None, on_neumann=None, stream=None, timeout=-1.0):
+          block_size=0, normals=None, on_neumann=None, stream=None, timeout=-1.0, sigma=0.0, screen_after=0):
     """Runs a solve to completion; returns a dict of per-point statistics."""
     h = wost_solve(scene.handle, points, walks, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                   normals, on_neumann, stream)
+                   normals, on_neumann, stream, sigma, screen_after)
     try:
         wost_wait(h, timeout)
         mean, se, wd, prog = wost_poll(h, points.shape[0])
@@ -496,3 +503,15 @@ def wost_solve_static(scene, points, walks_per_point, epsilon, r_min, max_steps,
                                     float(epsilon), float(r_min), int(max_steps), int(seed), int(first_walk),
                                     mean_out.data_ptr(), None if stderr_out is None else stderr_out.data_ptr(),
                                     _stream_ptr(stream)))
+
+
+def wost_screened_kernels(dim, rho, R, sigma, stream=None):
+    """G^sigma_B and Q^sigma_B (App. A.2) at CUDA float32 tensors rho, R;
+    returns (G, Q) as new CUDA tensors."""
+    import torch
+
+    G = torch.empty_like(rho)
+    Q = torch.empty_like(rho)
+    _check(load().wost_screened_kernels(int(dim), int(rho.numel()), _dptr(rho), _dptr(R), float(sigma), _dptr(G),
+                                        _dptr(Q), _stream_ptr(stream)))
+    return G, Q

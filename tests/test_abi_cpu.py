@@ -49,7 +49,6 @@ def _good():
     (lambda s: s["prims"].__setitem__((2, 0), -1), "negative index"),
     (lambda s: s["flags"].__setitem__(5, 2), "flag"),
     (lambda s: s["vertices"].__setitem__((1, 0), np.nan), "non-finite"),
-    (lambda s: s.update(flags=np.ones(16, np.uint8)), "no Dirichlet"),
     (lambda s: s.update(g={"kind": "per_vertex", "values": None}), "missing values"),
     (lambda s: s.update(g={"kind": "analytic", "fn": "exp_cos", "params": []}, f={"kind": "per_vertex", "values": np.zeros(16)}), "f per vertex"),
     (lambda s: s.update(h={"kind": "grid", "values": np.zeros(4), "origin": [0, 0], "spacing": [1, 1], "dims": [2, 2]}), "h grid"),
