@@ -5,9 +5,12 @@ Dirichlet, half Neumann by arc length) with a 1024-segment random-walk hole
 (all Neumann); exact u = sin 2x cos 3y, f = 13 u; the interior cell centres of
 a 512 x 512 raster (139,674 points), 256 walks per point, eps = r_min = 1e-4.
 The whole workload is about 1.1e11 walk steps (walks average ~3,000 steps:
-most of the boundary reflects).  A step is one strided batch of it: every
-16th grid point (~8,730 points, ~2.2 million walks, far more than the GPU's
-resident threads) with all 256 walks; 16 steps cover the grid.
+most of the boundary reflects; the longest reach the 65,536-step cap).  It
+runs as one resumable solve over the whole grid, and a step is one launch of
+it: every resident lane runs up to --iters walk steps, drawing new walks as
+its walks end and carrying unfinished ones to the next launch, so no launch
+waits for the longest walks.  The e2e figure is complete solves of every
+16th grid point from host memory, the longest walks included.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 

@@ -77,8 +77,10 @@ typedef enum {
     WOST_FN_QUAD3 = 3,       /* u = x^2 - y^2 + z/2                            */
     WOST_FN_BUMP = 4,        /* u = (1 - |x|^2)/(2 dim), -Lap u = 1            */
     WOST_FN_LINEAR = 5,      /* u = p0 + p1 x + p2 y + p3 z                    */
-    WOST_FN_LOG_RADIAL = 6   /* 2D p0 + p1 log|x-c|, 3D p0 + p1/|x-c|,
+    WOST_FN_LOG_RADIAL = 6,  /* 2D p0 + p1 log|x-c|, 3D p0 + p1/|x-c|,
                                 c = (p2, p3, p4)                               */
+    WOST_FN_EXP_PLANE = 7    /* u = p0 exp(p1 x + p2 y + p3 z): solves the
+                                screened equation for sigma = p1^2+p2^2+p3^2   */
 } wost_fn;
 
 typedef struct {

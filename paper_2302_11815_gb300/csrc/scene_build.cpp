@@ -395,7 +395,7 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
             return "";
         }
         case WOST_DATA_ANALYTIC:
-            if (f.fn < WOST_FN_ZERO || f.fn > WOST_FN_LOG_RADIAL) return "unknown analytic function id";
+            if (f.fn < WOST_FN_ZERO || f.fn > WOST_FN_EXP_PLANE) return "unknown analytic function id";
             return "";
         case WOST_DATA_GRID: {
             if (!is_source) return "GRID is only valid for f";

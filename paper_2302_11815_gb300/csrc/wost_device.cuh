@@ -964,8 +964,11 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     P3 xq = w.onN ? w.x - w.n * delta : w.x;
     // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
     float dsil = q.silhouette(sc.S, xq, dD);
-    // (R14: at most the scene's diameter, which matters without Dirichlet data)
-    float r = fminf(fminf(dD, fmaxf(sp.r_min, dsil)), sc.rmax);
+    float r = fminf(dD, fmaxf(sp.r_min, dsil));
+    // R14: at most the scene's diameter, which matters only without Dirichlet
+    // data; such scenes are solved with sigma > 0, i.e. in the screened
+    // instantiation (with Dirichlet data, r <= d_D <= the diameter anyway)
+    if constexpr (SCR) r = fminf(r, sc.rmax);
     // screening of this step (R15: from step screen_after on)
     float sqs = 0.f;
     if constexpr (SCR) sqs = (sp.sigma > 0.f && w.steps - 1 >= sp.screen_after) ? sp.sqrt_sigma : 0.f;

@@ -24,7 +24,8 @@ _lock = threading.Lock()
 OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_BUDGET, ERR_CUDA, ERR_TIMEOUT, ERR_CANCELLED, ERR_INTERNAL = range(8)
 STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "BUDGET", "CUDA", "TIMEOUT", "CANCELLED", "INTERNAL"]
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
-FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6}
+FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6,
+      "exp_plane": 7}
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL = {"plain": 0, "persistent": 1, "counting": 2, "resumable": 3}
 COUNT_NAMES = ("q1", "q2", "q3", "q4", "vis")
