@@ -1,0 +1,80 @@
+// Screened walk kernels (the SCR = true instantiations of wost_walk.cuh:
+// -Lap u + sigma u = f, App. A.2), the batched kernel (whose jobs may be
+// screened or not), the evaluation kernel of the screened Green's function
+// and step weight, and their launchers (sm_103a).
+#include <cuda_runtime.h>
+
+#include "wost_screened.cuh"
+#include "wost_walk.cuh"
+
+namespace wost {
+
+// Eqs. GreensFnsScreenedPoissonBall and ScreenedPoissonKernelsSphere at n
+// (rho, R) pairs: the functions the screened walks evaluate (App. A.2)
+template <int D>
+__global__ void k_screened_kernels(int64_t n, const float *rho, const float *R, float sqs, float *G, float *Q) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float r = rho[i], RR = R[i];
+    if (G) G[i] = screened_green<D>(r, RR, sqs);
+    if (Q) Q[i] = screened_q<D>(r, RR, sqs);
+}
+
+cudaError_t launch_screened_kernels(int dim, int64_t n, const float *rho, const float *R, float sigma, float *G,
+                                    float *Q, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    unsigned grid = (unsigned)((n + block - 1) / block);
+    float sqs = sqrtf(sigma);
+    if (dim == 2)
+        k_screened_kernels<2><<<grid, block, 0, s>>>(n, rho, R, sqs, G, Q);
+    else
+        k_screened_kernels<3><<<grid, block, 0, s>>>(n, rho, R, sqs, G, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk_plain_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
+                                  cudaStream_t s) {
+    return walk_plain_launch<true>(sc, sp, acc, block, s);
+}
+cudaError_t launch_walk_count_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                                  unsigned long long *stats, int block, cudaStream_t s) {
+    return walk_count_launch<true>(sc, sp, acc, stats, block, s);
+}
+cudaError_t launch_walk_persistent_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                                       int block, int blocks, cudaStream_t s) {
+    return walk_persistent_launch<true>(sc, sp, acc, block, blocks, s);
+}
+cudaError_t launch_walk_resume_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                                   const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
+    return walk_resume_launch<true>(sc, sp, acc, rs, iters, block, blocks, s);
+}
+
+cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t sm = smem_bytes(depth, block);
+    if (e == cudaSuccess && sm > 48 * 1024)
+        e = dim == 2 ? cudaFuncSetAttribute(k_walk_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                     : cudaFuncSetAttribute(k_walk_batch<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess)
+        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<2>, block, sm)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<3>, block, sm);
+    if (e != cudaSuccess) return e;
+    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
+    return cudaSuccess;
+}
+
+cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
+                              unsigned int *guard, int depth, const int *cancel, int block, int blocks,
+                              cudaStream_t s) {
+    size_t sm = smem_bytes(depth, block);
+    if (dim == 2)
+        k_walk_batch<2><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
+    else
+        k_walk_batch<3><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
+    return cudaGetLastError();
+}
+
+}  // namespace wost

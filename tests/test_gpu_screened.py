@@ -68,7 +68,8 @@ def test_walk_screened_disk_against_exact_and_oracle(wost, kernel, neumann_frac)
     check_z(res["mean"] - u, res["se"], 3e-3, label=f"gpu screened disk N={neumann_frac}")
     o = oracle.solve(oracle.Scene(sc), pts[:16], 600, 1e-3, max_steps=4096, seed=3, sigma=sig)
     se = np.hypot(o["se"], res["se"][:16])
-    check_z(res["mean"][:16] - o["mean"], se, 0.0, label="gpu vs oracle screened")
+    # 16 points: the outlier rule only (their mean z^2 scatters too much for a band)
+    check_z(res["mean"][:16] - o["mean"], se, 0.0, band=None, label="gpu vs oracle screened")
 
 
 def test_walk_screened_cube_3d(wost):
