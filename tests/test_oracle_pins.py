@@ -543,3 +543,23 @@ def test_walk_screened_cube_exp_plane_3d():
     r = oracle.solve(O, pts, 1500, 1e-3, max_steps=4096, seed=29, sigma=sig)
     u = scenes.exact_u("exp_plane", (1.0, *a), pts)
     check_z(r["mean"] - u, r["se"], 1e-3 * 4.0, label="screened cube")
+
+
+@pytest.mark.parametrize("where", ["mid", "near_end"])
+def test_walk_from_points_on_the_neumann_boundary(where):
+    # Alg. 1 admits x0 on the Neumann boundary (its normal n_x given): the
+    # first step samples the hemisphere about -n_x and weights the Neumann
+    # term with alpha = 1/2 (R8).  Points on Neumann segments of the flower
+    # scene, against the exact solution.
+    sc = scenes.config1()
+    V = sc["vertices"].astype(np.float64)
+    P = sc["prims"]
+    nrm = scenes.prim_normals(sc)
+    odd = np.nonzero(sc["flags"] == 1)[0][::4]
+    s = 0.5 if where == "mid" else 0.9
+    pts = V[P[odd, 0]] * (1 - s) + V[P[odd, 1]] * s
+    O = oracle.Scene(sc)
+    r = oracle.solve(O, pts, 3000, 1e-3, max_steps=1024, seed=41, normals=nrm[odd], on_neumann=np.ones(len(odd)))
+    u = scenes.exact_u("exp_cos", (), pts)
+    # (alpha = 1 instead of 1/2 at these points fails this check)
+    check_z(r["mean"] - u, r["se"], 1e-3 * 3.0, label=f"boundary points {where}")
