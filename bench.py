@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -112,7 +113,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        out = os.environ.get("WOST_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"wost_clocks_gpu{gpu_index}.csv")
 
     def start(self):
         try:
