@@ -136,6 +136,15 @@ typedef struct {
  * OUT_OF_MEMORY; CUDA.  A scene without Dirichlet primitives (a pure
  * Neumann problem, Sec. 6.4) is accepted; its solves need sigma > 0. */
 wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out);
+
+/* Builds the hierarchies of a scene on the host only (no device is used),
+ * checks their structure -- every child reference reaches a node once or a
+ * leaf, every primitive lies in exactly one leaf, every box contains what
+ * lies below it, every normal cone of the silhouette hierarchy contains the
+ * normals below it, no leaf is deeper than the traversal stacks are sized
+ * for; binary and 8-wide forms -- and fills *info (device_bytes = 0).
+ * Errors: INVALID_ARG as wost_scene_create; INTERNAL with the violation. */
+wost_status wost_scene_validate(const wost_scene_desc *desc, wost_scene_info *info);
 wost_status wost_scene_destroy(wost_scene *scene);
 wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out);
 

@@ -40,4 +40,8 @@ struct HostScene {
 // empty string on success, else the reason for rejecting the input.
 std::string build_scene(const wost_scene_desc &desc, HostScene &out);
 
+// Structural checks of the built hierarchies (scene_check.cpp): empty string
+// when they hold, else the first violation.
+std::string check_scene(const HostScene &scene);
+
 }  // namespace wost

@@ -161,6 +161,47 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
     }
 }
 
+wost_status wost_scene_validate(const wost_scene_desc *desc, wost_scene_info *out) {
+    try {
+        if (!desc || !out) return fail(WOST_ERR_INVALID_ARG, "null argument");
+        HostScene H;
+        std::string err = build_scene(*desc, H);
+        if (!err.empty()) return fail(WOST_ERR_INVALID_ARG, err);
+        err = check_scene(H);
+        if (!err.empty()) return fail(WOST_ERR_INTERNAL, err);
+        wost_scene_info I{};
+        I.dim = H.dim;
+        I.n_dirichlet = H.n_dirichlet;
+        I.n_neumann = H.n_neumann;
+        I.n_silhouette = H.n_silhouette;
+        I.n_dropped = H.n_dropped;
+        I.nodes_dirichlet = H.D.n_nodes;
+        I.nodes_neumann = H.N.n_nodes;
+        I.nodes_silhouette = H.S.n_nodes;
+        I.depth_dirichlet = H.D.depth;
+        I.depth_neumann = H.N.depth;
+        I.depth_silhouette = H.S.depth;
+        I.lanes_per_walk = WOST_TEAM;
+        I.wide_nodes_dirichlet = H.D.wn_nodes;
+        I.wide_nodes_neumann = H.N.wn_nodes;
+        I.wide_nodes_silhouette = H.S.wn_nodes;
+        I.wide_depth_dirichlet = H.D.wdepth;
+        I.wide_depth_neumann = H.N.wdepth;
+        I.wide_depth_silhouette = H.S.wdepth;
+        I.build_seconds = H.build_seconds;
+        for (int a = 0; a < 3; ++a) {
+            I.bbox_lo[a] = H.lo[a];
+            I.bbox_hi[a] = H.hi[a];
+        }
+        *out = I;
+        return WOST_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(WOST_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(WOST_ERR_INTERNAL, e.what());
+    }
+}
+
 wost_status wost_scene_destroy(wost_scene *scene) {
     if (!scene) return fail(WOST_ERR_INVALID_ARG, "null scene");
     cudaSetDevice(scene->device);

@@ -79,6 +79,7 @@ class wost_progress(C.Structure):
 _SIGS = {
     "wost_scene_create": [C.POINTER(wost_scene_desc), C.POINTER(C.c_void_p)],
     "wost_scene_destroy": [C.c_void_p],
+    "wost_scene_validate": [C.POINTER(wost_scene_desc), C.POINTER(wost_scene_info)],
     "wost_scene_get_info": [C.c_void_p, C.POINTER(wost_scene_info)],
     "wost_solve": [C.c_void_p, C.POINTER(wost_solve_desc), C.POINTER(C.c_void_p)],
     "wost_poll": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(wost_progress)],
@@ -191,10 +192,7 @@ def _stream_ptr(stream):
 # ---------------------------------------------------------------------------
 # C calls with the same names
 # ---------------------------------------------------------------------------
-def wost_scene_create(spec: dict, device: int = 0, leaf_size: int = 0):
-    """Creates a scene from a scene dict (see scenes.py); returns the handle."""
-    lib = load()
-    keep = []
+def _scene_desc(spec: dict, device: int, leaf_size: int, keep: list):
     dim = int(spec["dim"])
     V = np.ascontiguousarray(spec["vertices"], np.float32)
     P = np.ascontiguousarray(spec["prims"], np.int32)
@@ -212,9 +210,31 @@ def wost_scene_create(spec: dict, device: int = 0, leaf_size: int = 0):
     d.f = _field(spec.get("f"), keep)
     d.device = device
     d.leaf_size = leaf_size
+    return d
+
+
+def wost_scene_create(spec: dict, device: int = 0, leaf_size: int = 0):
+    """Creates a scene from a scene dict (see scenes.py); returns the handle."""
+    lib = load()
+    keep = []
+    d = _scene_desc(spec, device, leaf_size, keep)
     h = C.c_void_p()
     _check(lib.wost_scene_create(C.byref(d), C.byref(h)))
     return h
+
+
+def wost_scene_validate(spec: dict, leaf_size: int = 0) -> dict:
+    """Builds a scene's hierarchies on the host only and checks their
+    structure; returns the scene info (raises WostError on a violation)."""
+    lib = load()
+    keep = []
+    d = _scene_desc(spec, 0, leaf_size, keep)
+    info = wost_scene_info()
+    _check(lib.wost_scene_validate(C.byref(d), C.byref(info)))
+    out = {k: getattr(info, k) for k, _ in wost_scene_info._fields_}
+    out["bbox_lo"] = list(info.bbox_lo)
+    out["bbox_hi"] = list(info.bbox_hi)
+    return out
 
 
 def wost_scene_destroy(h):

@@ -89,3 +89,38 @@ def test_null_arguments(lib):
     assert lib.wost_solve_destroy(None) == wost.ERR_INVALID_ARG
     assert lib.wost_scene_destroy(None) == wost.ERR_INVALID_ARG
     assert lib.wost_query_closest_dirichlet(None, 1, None, None, None, None, None) == wost.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,leaf", [("config1", 0), ("config1", 1), ("config1", 16), ("koch3_hole", 0),
+                                       ("annulus", 0), ("square", 2), ("cube", 0), ("box_sphere", 0),
+                                       ("box_sphere", 8), ("torus_small", 0), ("pure_neumann_disk", 0)])
+def test_scene_hierarchies_are_well_formed(lib, name, leaf):
+    # host-only build and structural check (no GPU): references, coverage of
+    # every record by exactly one leaf, nested boxes, silhouette cones that
+    # contain the normals below them, depth within the stack sizing
+    from paper_2302_11815_gb300 import wost
+
+    if name == "config1":
+        sc = scenes.config1()
+    elif name == "koch3_hole":
+        sc = scenes.config2(grid=8, level=3)
+    elif name == "annulus":
+        sc = scenes.annulus_scene()
+    elif name == "square":
+        sc = scenes.square_scene(m=16)
+    elif name == "cube":
+        sc = scenes.cube_scene(m=8, neumann_faces=(1, 4))
+    elif name == "box_sphere":
+        sc = scenes.box_sphere_scene()
+    elif name == "torus_small":
+        sc = scenes.config3(grid=4, nu=60, nv=24, cube_m=4)
+    else:
+        sc = scenes.disk_scene(64, "exp_plane", (1.0, 0.5, 0.2, 0.0), neumann=np.ones(64, bool))
+    info = wost.wost_scene_validate(sc, leaf_size=leaf)
+    n = len(sc["prims"])
+    assert info["n_dirichlet"] + info["n_neumann"] + info["n_dropped"] == n
+    if info["n_dropped"] == 0:
+        assert info["n_dirichlet"] == int((sc["flags"] == 0).sum())
+    if info["n_dirichlet"]:
+        assert info["depth_dirichlet"] >= 1 and info["wide_depth_dirichlet"] >= 1
+    assert info["n_silhouette"] >= 1 and info["depth_silhouette"] >= 1
