@@ -563,3 +563,31 @@ def test_walk_from_points_on_the_neumann_boundary(where):
     u = scenes.exact_u("exp_cos", (), pts)
     # (alpha = 1 instead of 1/2 at these points fails this check)
     check_z(r["mean"] - u, r["se"], 1e-3 * 3.0, label=f"boundary points {where}")
+
+
+def test_walk_screened_pure_neumann_cube_3d():
+    # every face Neumann: well posed only for sigma > 0; walks end by roulette
+    a = (0.7, 0.3, -0.5)
+    sig = sum(t * t for t in a)
+    sc = scenes.cube_scene(m=4, fn="exp_plane", params=(1.0, *a), neumann_faces=(0, 1, 2, 3, 4, 5))
+    O = oracle.Scene(sc)
+    pts = np.random.default_rng(8).uniform(-0.8, 0.8, size=(16, 3))
+    r = oracle.solve(O, pts, 2000, 1e-3, max_steps=4096, seed=31, sigma=sig)
+    assert r["capped"].sum() == 0
+    check_z(r["mean"] - scenes.exact_u("exp_plane", (1.0, *a), pts), r["se"], 0.0, label="screened Neumann cube")
+
+
+def test_walk_from_points_on_a_neumann_sphere_3d():
+    # starts on the inner Neumann sphere of the box-sphere scene (normals out
+    # of the domain, i.e. into the sphere), against the exact solution
+    sc = scenes.box_sphere_scene(data="analytic")
+    nrm = scenes.prim_normals(sc)
+    V = sc["vertices"].astype(np.float64)
+    P = sc["prims"]
+    sphere = np.nonzero(sc["flags"] == 1)[0][::37]
+    pts = (V[P[sphere, 0]] + V[P[sphere, 1]] + V[P[sphere, 2]]) / 3.0
+    O = oracle.Scene(sc)
+    r = oracle.solve(O, pts, 2000, 1e-3, max_steps=1024, seed=43, normals=nrm[sphere],
+                     on_neumann=np.ones(len(sphere)))
+    u = scenes.exact_u("quad3", (), pts)
+    check_z(r["mean"] - u, r["se"], 1e-3 * 3.0, label="boundary points on a sphere")
