@@ -124,3 +124,15 @@ def test_scene_hierarchies_are_well_formed(lib, name, leaf):
     if info["n_dirichlet"]:
         assert info["depth_dirichlet"] >= 1 and info["wide_depth_dirichlet"] >= 1
     assert info["n_silhouette"] >= 1 and info["depth_silhouette"] >= 1
+
+
+def test_batched_workload_scenes_are_well_formed(lib):
+    # the batched workload's generator (2D radial polygons with holes, 3D
+    # cube + torus), scenes capped at 20k primitives here: every scene
+    # builds and passes the structural checks
+    from paper_2302_11815_gb300 import wost
+
+    for sc in scenes.config4(n_scenes=12, points=(1, 64), max_scene=20000):
+        info = wost.wost_scene_validate(sc)
+        assert info["n_dirichlet"] > 0 and info["n_neumann"] > 0
+        assert info["n_dirichlet"] + info["n_neumann"] + info["n_dropped"] == len(sc["prims"])
