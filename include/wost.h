@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define WOST_ABI_VERSION 1
+#define WOST_ABI_VERSION 2
 
 typedef enum {
     WOST_OK = 0,

@@ -26,6 +26,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "BUDGET", "CUDA", "TIMEOUT
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
 FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6,
       "exp_plane": 7}
+ABI_VERSION = 2  # WOST_ABI_VERSION of the header these structures mirror
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL = {"plain": 0, "persistent": 1, "counting": 2, "resumable": 3}
 COUNT_NAMES = ("q1", "q2", "q3", "q4", "vis")
@@ -126,6 +127,9 @@ def load(path: str | None = None):
             lib.wost_last_error.restype = C.c_char_p
             lib.wost_last_error.argtypes = []
             lib.wost_abi_version.restype = C.c_int32
+            if lib.wost_abi_version() != ABI_VERSION:
+                raise OSError(f"{p}: ABI version {lib.wost_abi_version()}, this binding needs {ABI_VERSION}; "
+                              "rebuild the library")
             _lib = lib
     return _lib
 
