@@ -17,10 +17,31 @@ Parity status of the functions (what pins them, see tests/test_oracle_*.py):
                     subdivision independence of a straight wall, 3D edge
   intersect_neumann hand-derived hits on segments / triangles
   neumann_sample    E[1/pdf] = measure of the Neumann boundary in the ball
+  silhouette_distance_tol, intersect_neumann_tol
+                    (test-only threshold brackets) reduce to the two
+                    functions above at 0 and are monotone in the threshold
   solve / walk      exact harmonic and Poisson solutions (pure Dirichlet =
                     walk on spheres, mixed Dirichlet/Neumann, sources,
                     3D), arc harmonic measure (Poisson kernel of the disk),
                     1/sqrt(N) convergence
+
+Boundary data and analytic solutions, and the pins that exercise each:
+  data none         f absent in every source-free walk pin
+  data analytic     every exact-solution walk pin below
+  data per_corner   Poisson kernel of the disk (indicator g), cube around a
+                    Neumann sphere (quad3 g and h), per-vertex equivalence
+  data per_vertex   linear u on a square (2D) and on a cube with a Neumann
+                    face (3D): exact; equal to per-corner walk for walk
+  data grid         screened source on a grid (bilinear, clamped)
+  fn zero           Poisson kernel of the disk
+  fn exp_cos        pure Dirichlet disk, the 64-segment flower, convergence
+  fn sin2x_cos3y    f = 13 u on a Dirichlet disk and with a Neumann half
+  fn quad3          pure Dirichlet cube, cube around a Neumann sphere
+  fn bump           -Lap u = 1 in 2D and 3D (sign and norm of the source)
+  fn linear         square with Neumann sides, per-vertex pins, R13
+  fn log_radial     annulus with a Neumann inner circle
+  fn exp_plane      screened disks and cubes (Dirichlet, mixed, pure Neumann)
+No function of the oracle is unpinned.
 """
 from __future__ import annotations
 
@@ -84,6 +105,8 @@ def _L():
             lib.orc_closest_dirichlet.argtypes = [P, C.c_int64, P, P, P, P]
             lib.orc_silhouette_distance.argtypes = [P, C.c_int64, P, P, P, P]
             lib.orc_intersect_neumann.argtypes = [P, C.c_int64, P, P, P, P, P, P, P]
+            lib.orc_silhouette_distance_tol.argtypes = [P, C.c_int64, P, P, C.c_double, P]
+            lib.orc_intersect_neumann_tol.argtypes = [P, C.c_int64, P, P, P, P, C.c_double, P, P]
             lib.orc_neumann_sample.argtypes = [P, P, C.c_double, C.c_uint64, C.c_uint32,
                                                C.c_uint32, C.c_uint32, P, P, P, P]
             lib.orc_green_ball.restype = C.c_double
@@ -216,6 +239,30 @@ def intersect_neumann(scene: Scene, origins, dirs, tmax, skip=None):
     _L().orc_intersect_neumann(scene._h, n, _ptr(o), _ptr(v), _ptr(tm), _ptr(sk), _ptr(hit),
                                _ptr(t), _ptr(pr))
     return hit.astype(bool), t, pr
+
+
+def silhouette_distance_tol(scene: Scene, pts, rmax, tau):
+    """Q.2 with the silhouette threshold moved to tau |v| (1 + |x|_inf)
+    (tests only: brackets answers decided in single precision)."""
+    x = _d(pts)
+    n = len(x)
+    rm = _d(np.broadcast_to(np.asarray(rmax, np.float64), (n,)))
+    d = np.zeros(n)
+    _L().orc_silhouette_distance_tol(scene._h, n, _ptr(x), _ptr(rm), float(tau), _ptr(d))
+    return d
+
+
+def intersect_neumann_tol(scene: Scene, origins, dirs, tmax, tol, skip=None):
+    """Q.3 with the accepted segment-parameter / barycentric range widened
+    by tol (tests only: brackets answers decided in single precision)."""
+    o = _d(origins); v = _d(dirs)
+    n = len(o)
+    tm = _d(np.broadcast_to(np.asarray(tmax, np.float64), (n,)))
+    sk = None if skip is None else np.ascontiguousarray(np.broadcast_to(skip, (n,)), np.int32)
+    hit = np.zeros(n, np.int32); t = np.zeros(n)
+    _L().orc_intersect_neumann_tol(scene._h, n, _ptr(o), _ptr(v), _ptr(tm), _ptr(sk), float(tol), _ptr(hit),
+                                   _ptr(t))
+    return hit.astype(bool), t
 
 
 def neumann_sample(scene: Scene, x, r, seed=0, c0=0, c1=0, c2=0):

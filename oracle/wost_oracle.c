@@ -605,8 +605,11 @@ static V3 closest_on_prim(const orc_scene *s, int p, V3 x, double bary[3]) {
     return bq;
 }
 
-/* first intersection of the ray o + t v, 0 < t <= tmax, with primitive p */
-static int ray_prim(const orc_scene *s, int p, V3 o, V3 v, double tmax, double *t_out) {
+/* first intersection of the ray o + t v, 0 < t <= tmax, with primitive p.
+ * tol widens (> 0) or narrows (< 0) the accepted range of the segment
+ * parameter / barycentric coordinates; the walk uses the exact test, tol = 0
+ * (the parity tests bracket a single-precision answer between tol = +-tau) */
+static int ray_prim(const orc_scene *s, int p, V3 o, V3 v, double tmax, double *t_out, double tol) {
     V3 a = corner(s, p, 0), b = corner(s, p, 1);
     if (s->dim == 2) {
         V3 e = sub(b, a), ao = sub(a, o);
@@ -614,7 +617,7 @@ static int ray_prim(const orc_scene *s, int p, V3 o, V3 v, double tmax, double *
         if (den == 0) return 0;
         double t = (ao.x * e.y - ao.y * e.x) / den;
         double u = (ao.x * v.y - ao.y * v.x) / den;
-        if (u < 0 || u > 1 || t <= 0 || t > tmax) return 0;
+        if (u < -tol || u > 1 + tol || t <= 0 || t > tmax) return 0;
         *t_out = t;
         return 1;
     }
@@ -627,10 +630,10 @@ static int ray_prim(const orc_scene *s, int p, V3 o, V3 v, double tmax, double *
     double inv = 1.0 / det;
     V3 tv = sub(o, a);
     double u = dot(tv, pv) * inv;
-    if (u < 0 || u > 1) return 0;
+    if (u < -tol || u > 1 + tol) return 0;
     V3 qv = crs(tv, e1);
     double w = dot(v, qv) * inv;
-    if (w < 0 || u + w > 1) return 0;
+    if (w < -tol || u + w > 1 + tol) return 0;
     double t = dot(e2, qv) * inv;
     if (t <= 0 || t > tmax) return 0;
     *t_out = t;
@@ -725,13 +728,17 @@ static double q_closest_dirichlet(const orc_scene *s, V3 x, V3 *xbar, int *prim,
     return best;
 }
 
-static int is_silhouette(const orc_scene *s, int k, V3 v) {
+/* Eq. SilhouetteDefinition at the candidate point pe = x + v: (v.n0)(v.n1) <=
+ * 0.  tau relaxes (> 0) or tightens (< 0) the threshold to tau |v| (1 +
+ * |x|_inf), the size of single-precision rounding in the product; the walk
+ * uses tau = 0 */
+static int is_silhouette(const orc_scene *s, int k, V3 v, double tau) {
     if (s->snadj[k] != 2) return 1; /* boundary (or non-manifold) edge/vertex */
     double a = dot(v, s->nrm[s->sf0[k]]), b = dot(v, s->nrm[s->sf1[k]]);
-    return a * b <= 0;
+    return a * b <= tau;
 }
 
-static double q_silhouette(const orc_scene *s, V3 x, double rmax, int *which) {
+static double q_silhouette_tol(const orc_scene *s, V3 x, double rmax, int *which, double tau) {
     double best = rmax;
     *which = -1;
     for (int k = 0; k < s->nsil; ++k) {
@@ -744,16 +751,20 @@ static double q_silhouette(const orc_scene *s, V3 x, double rmax, int *which) {
         }
         V3 v = sub(pe, x);
         double d = len(v);
-        if (d < best && is_silhouette(s, k, v)) {
+        double scale = 1.0 + fmax(fabs(x.x), fmax(fabs(x.y), fabs(x.z)));
+        if (d < best && is_silhouette(s, k, v, tau * d * scale)) {
             best = d;
             *which = k;
         }
     }
     return best;
 }
+static double q_silhouette(const orc_scene *s, V3 x, double rmax, int *which) {
+    return q_silhouette_tol(s, x, rmax, which, 0.0);
+}
 
-static int q_intersect_neumann(const orc_scene *s, V3 o, V3 v, double tmax, int skip, double *t_out,
-                               int *prim) {
+static int q_intersect_neumann_tol(const orc_scene *s, V3 o, V3 v, double tmax, int skip, double *t_out,
+                                   int *prim, double tol) {
     double best = tmax;
     int hit = 0;
     *prim = -1;
@@ -761,7 +772,7 @@ static int q_intersect_neumann(const orc_scene *s, V3 o, V3 v, double tmax, int 
         int p = s->Nl[i];
         if (p == skip) continue;
         double t;
-        if (ray_prim(s, p, o, v, best, &t)) {
+        if (ray_prim(s, p, o, v, best, &t, tol)) {
             best = t;
             hit = 1;
             *prim = p;
@@ -769,6 +780,10 @@ static int q_intersect_neumann(const orc_scene *s, V3 o, V3 v, double tmax, int 
     }
     *t_out = best;
     return hit;
+}
+static int q_intersect_neumann(const orc_scene *s, V3 o, V3 v, double tmax, int skip, double *t_out,
+                               int *prim) {
+    return q_intersect_neumann_tol(s, o, v, tmax, skip, t_out, prim, 0.0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -871,6 +886,27 @@ void orc_silhouette_distance(const orc_scene *s, int64_t n, const double *x, con
         int w;
         out_d[i] = q_silhouette(s, load_pt(s->dim, x, i), rmax[i], &w);
         out_sil[i] = w;
+    }
+}
+/* the same brute-force queries with relaxed / tightened thresholds (tests
+ * only: a single-precision answer decided within rounding of a threshold
+ * must lie between the answers for -tau and +tau) */
+void orc_silhouette_distance_tol(const orc_scene *s, int64_t n, const double *x, const double *rmax,
+                                 double tau, double *out_d) {
+    for (int64_t i = 0; i < n; ++i) {
+        int w;
+        out_d[i] = q_silhouette_tol(s, load_pt(s->dim, x, i), rmax[i], &w, tau);
+    }
+}
+void orc_intersect_neumann_tol(const orc_scene *s, int64_t n, const double *o, const double *v,
+                               const double *tmax, const int32_t *skip, double tol, int32_t *out_hit,
+                               double *out_t) {
+    for (int64_t i = 0; i < n; ++i) {
+        double t;
+        int p;
+        out_hit[i] = q_intersect_neumann_tol(s, load_pt(s->dim, o, i), load_pt(s->dim, v, i), tmax[i],
+                                             skip ? skip[i] : -1, &t, &p, tol);
+        out_t[i] = t;
     }
 }
 void orc_intersect_neumann(const orc_scene *s, int64_t n, const double *o, const double *v,

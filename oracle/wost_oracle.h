@@ -92,6 +92,18 @@ void orc_intersect_neumann(const orc_scene *s, int64_t n, const double *o,
                            const int32_t *skip, int32_t *out_hit,
                            double *out_t, int32_t *out_prim);
 
+/* Q.2 and Q.3 with the silhouette threshold moved to tau |v| (1 + |x|_inf)
+ * (Q.2) or the segment-parameter / barycentric range widened by tol (Q.3):
+ * positive values accept more, negative fewer.  Tests only: an answer
+ * decided in single precision within rounding of a threshold lies between
+ * the answers for a negative and a positive value. */
+void orc_silhouette_distance_tol(const orc_scene *s, int64_t n, const double *x,
+                                 const double *rmax, double tau, double *out_d);
+void orc_intersect_neumann_tol(const orc_scene *s, int64_t n, const double *o,
+                               const double *v, const double *tmax,
+                               const int32_t *skip, double tol, int32_t *out_hit,
+                               double *out_t);
+
 /* Q.4 hierarchical Neumann sample (Algs. 5-6) for ball (x, r) with uniforms
  * drawn from the Philox stream (seed, ctr0, ctr1, ctr2, slot 1...).  Writes
  * z [3], n_z [3], pdf and the primitive (or -1). */

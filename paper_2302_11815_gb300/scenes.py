@@ -194,7 +194,44 @@ def point_in_polygon(pts: np.ndarray, poly: np.ndarray) -> np.ndarray:
     return (np.count_nonzero(cross, axis=1) % 2) == 1
 
 
+def _star_angles(poly: np.ndarray):
+    """Vertex angles about the origin sorted ascending with the matching
+    vertex order, if the polygon is star-shaped about the origin with its
+    vertices in angular order (either orientation); else None."""
+    th = np.arctan2(poly[:, 1], poly[:, 0])
+    if np.any(np.hypot(poly[:, 0], poly[:, 1]) == 0):
+        return None
+    order = np.argsort(th, kind="stable")
+    n = len(poly)
+    # in angular order the polygon's successor relation must be a rotation
+    pos = np.empty(n, int)
+    pos[order] = np.arange(n)
+    step = (pos[(np.arange(n) + 1) % n] - pos) % n
+    if not (np.all(step == 1) or np.all(step == n - 1)):
+        return None
+    return th[order], poly[order]
+
+
+def _inside_star(pts, th, V):
+    """Inside test for a polygon star-shaped about the origin: the ray from
+    the origin through p meets the boundary once, at the edge between the
+    two vertices whose angles bracket p's; p is inside iff it is nearer."""
+    n = len(V)
+    tp = np.arctan2(pts[:, 1], pts[:, 0])
+    k = (np.searchsorted(th, tp, side="right") - 1) % n
+    a, b = V[k], V[(k + 1) % n]
+    e = b - a
+    rho = np.hypot(pts[:, 0], pts[:, 1])
+    d = pts / np.maximum(rho, 1e-300)[:, None]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = (a[:, 0] * e[:, 1] - a[:, 1] * e[:, 0]) / (d[:, 0] * e[:, 1] - d[:, 1] * e[:, 0])
+    return rho < t
+
+
 def _inside_chunked(pts, poly, chunk=4096):
+    star = _star_angles(poly) if len(poly) > 256 else None
+    if star is not None:
+        return _inside_star(pts, *star)
     out = np.zeros(len(pts), bool)
     for s in range(0, len(pts), chunk):
         out[s:s + chunk] = point_in_polygon(pts[s:s + chunk], poly)
@@ -645,7 +682,7 @@ def config4(n_scenes=64, seed=4001, prims=(1e3, 5e5), points=(1, 1e6), walks=(16
         w = int(np.exp(rng.uniform(np.log(walks[0]), np.log(walks[1]))))
         f = rng.uniform(0.2, 0.8)
         if max_scene:
-            n_p = min(n_p, max_scene)
+            n_p = min(n_p, int(max_scene))
         out.append(batched_scene(i, n_p, dim, f, max(1, n_x), max(1, w), seed * 100 + i))
     return out
 
