@@ -1,16 +1,26 @@
 """Benchmark: walk-on-stars walk-steps/s on one or more GPUs.
 
-Workload: 2D Poisson on a level-5 Koch snowflake (3072 segments, half
-Dirichlet, half Neumann by arc length) with a 1024-segment random-walk hole
-(all Neumann); exact u = sin 2x cos 3y, f = 13 u; the interior cell centres of
-a 512 x 512 raster (139,674 points), 256 walks per point, eps = r_min = 1e-4.
-The whole workload is about 1.1e11 walk steps (walks average ~3,000 steps:
-most of the boundary reflects; the longest reach the 65,536-step cap).  It
-runs as one resumable solve over the whole grid, and a step is one launch of
-it: every resident lane runs up to --iters walk steps, drawing new walks as
-its walks end and carrying unfinished ones to the next launch, so no launch
-waits for the longest walks.  The e2e figure is complete solves of every
-16th grid point from host memory, the longest walks included.
+Headline workload: 2D Poisson on a level-5 Koch snowflake (3072 segments,
+half Dirichlet, half Neumann by arc length) with a 1024-segment random-walk
+hole (all Neumann); exact u = sin 2x cos 3y, f = 13 u; the interior cell
+centres of a 512 x 512 raster (141,021 points), 256 walks per point,
+eps = r_min = 1e-4.  The whole workload is about 1.1e11 walk steps (walks
+average ~3,000 steps: most of the boundary reflects; the longest reach the
+65,536-step cap).  It runs as one resumable solve over the whole grid, and a
+step is one launch of it: every resident lane runs up to --iters walk steps,
+drawing new walks as its walks end and carrying unfinished ones to the next
+launch, so no launch waits for the longest walks.  The e2e figure is a
+complete solve of every 16th grid point from host memory, the longest walks
+included.
+
+After the timed headline (N = 1 only) the same line carries the other
+workloads, measured outside the timed region: the 64-segment flower (plain
+and persistent launches), the 3D cube around a noisy 200k-triangle torus
+(resumable launches, its own work model and roofline), the batched
+multi-scene workload (one batched launch against one launch per scene, same
+walks) and the serving workload (a Poisson request stream into the engine:
+p50/p99 latency, offered against served load); plus the walks per point and
+points/s at which the headline workload reaches 1% relative RMS error.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -196,19 +206,78 @@ def work_per_step(counts, steps, dim, info):
     return b / steps, f / steps + STEP_FLOPS[dim]
 
 
-def measure_l2_read_gbs(torch, stream):
-    """Streaming-read bandwidth of a 64 MiB buffer resident in L2."""
-    x = torch.ones(16 << 20, dtype=torch.float32, device="cuda")
+def measure_read_gbs(torch, wost, stream, nbytes, passes, reps=5):
+    """Read bandwidth of the level a buffer of `nbytes` lives in, measured with
+    the library's read probe (16-byte loads that bypass L1, resident grid):
+    best of `reps` launches of `passes` sweeps, the first sweep of each
+    included, CUDA events on the launching stream."""
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    best = 0.0
     with torch.cuda.stream(stream):
-        for _ in range(5):
-            x.sum()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        for _ in range(50):
-            x.sum()
-        e.record(stream)
-    e.synchronize()
-    return 50 * x.numel() * 4 / (s.elapsed_time(e) * 1e-3) / 1e9
+        wost.wost_read_probe(buf, passes, sink, stream)
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wost.wost_read_probe(buf, passes, sink, stream)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, passes * nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
+    del buf
+    return best
+
+
+KERNEL_SOURCES = ("wost_device.cuh", "wost_walk.cuh", "wost_kernels.cu", "wost_internal.h")
+
+
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the sources the walk kernels compile
+    from: a profile taken of other sources does not describe this build."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2302_11815_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, src_hash):
+    """DRAM bytes per walk step of `kernel` from the ncu capture recorded in
+    profiles/traffic.txt (lines: kernel, source hash, dram bytes per walk
+    step, the capture), or None if none was taken of these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            f = line.split()
+            if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == src_hash:
+                return float(f[2])
+    return None
+
+
+def roofline_block(kernel, bytes_step, flops_step, steps, seconds, launches, peaks, peak_src, l2_gbs, hbm_probe_gbs,
+                   fp32, fp32_src, traffic_per_step, counts_per_step):
+    """Roofline of one kernel: the algorithmic bytes and flops per walk step
+    times the steps of the timed launches over their device time, against
+    the measured HBM copy bandwidth (the contract's memory roof), the L2 read
+    bandwidth measured here (the level the scenes live in, the stricter roof)
+    and the FP32 peak."""
+    achieved_b = bytes_step * steps / seconds / 1e9
+    achieved_f = flops_step * steps / seconds / 1e12
+    return {"bound": "hbm", "achieved": achieved_b, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved_b / peaks["hbm_gbs"],
+            "traffic": None if traffic_per_step is None else traffic_per_step * steps / launches,
+            "traffic_src": "DRAM bytes per launch: ncu dram__bytes_read + dram__bytes_write per walk step of this"
+                           " source build (profiles/traffic.txt) x the walk steps of an average timed launch",
+            "algorithmic_bytes_per_launch": bytes_step * steps / launches,
+            "kernel": kernel, "unit_of_work": "walk step", "bytes_per_step": bytes_step, "flops_per_step": flops_step,
+            "peak_src": peak_src, "l2_peak_gbs": l2_gbs, "l2_frac": achieved_b / l2_gbs,
+            "l2_peak_src": "measured in this run: read probe over a 48 MiB buffer (L2-resident)",
+            "hbm_probe_gbs": hbm_probe_gbs, "fp32_frac": achieved_f / fp32, "fp32_peak_tflops": fp32,
+            "fp32_peak_src": fp32_src, "achieved_tflops": achieved_f, "seconds": seconds, "steps": steps,
+            "counts_per_step": counts_per_step}
 
 
 def cpu_baseline(sc, walks=48, seed=1):
@@ -256,181 +325,125 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import torch
-
-    rank, world, local = _dist_init(args.gpus)
-    torch.cuda.set_device(local)
-    from paper_2302_11815_gb300 import scenes, wost
-
-    wost.load()  # fails loudly when the CUDA library is missing
-    sc = scenes.config2()
-    grid_pts = np.ascontiguousarray(sc["points"], np.float32)
-    walks = sc["walks"]
-    S = wost.Scene(sc, device=local)
-    info = S.info()
-    _log(f"scene built: {info['n_dirichlet']} D + {info['n_neumann']} N prims, {len(grid_pts)} grid points")
-    stream = torch.cuda.Stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    seed0 = 1000 * (rank + 1)
-
-    # work counts per step from the counting kernel on a subsample (untimed)
-    sub = torch.from_numpy(grid_pts[:: args.count_stride * 64].copy()).cuda()
-    r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting",
-                   timeout=600.0)
-    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2, info)
-    _log(f"work model: {r['total_steps']} steps counted, {bytes_step:.0f} B and {flops_step:.0f} flop per step")
-
-    # The job: every grid point x 256 walks (36 million walks, ~1.1e11 walk
-    # steps), device-resident, run as a resumable solve.  A bench step is
-    # one launch of it: every resident lane runs up to `iters` walk steps,
-    # drawing new walks as its walks end and carrying unfinished ones over.
-    pts_dev = torch.from_numpy(grid_pts).cuda()
-    job = wost.wost_solve(S.handle, pts_dev, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0,
-                          kernel="resumable", block_size=args.block, stream=stream)
-    n_all = len(grid_pts)
+def _resumable_launches(wost, torch, S, pts_dev, sc, stream, flush, iters, warmup, steps, seed, block=0):
+    """A resumable solve of every point x the workload's walks; `warmup`
+    untimed launches, then `steps` timed launches of `iters` walk steps per
+    lane, L2 flushed before each (outside the events).  Returns the solve
+    handle (open), the walk steps of the timed launches, their device
+    seconds and the per-launch milliseconds."""
+    job = wost.wost_solve(S.handle, pts_dev, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed,
+                          kernel="resumable", block_size=block, stream=stream)
+    n = pts_dev.shape[0]
 
     def steps_run():
-        return wost.wost_poll(job, n_all)[3]["steps_run"]
+        return wost.wost_poll(job, n)[3]["steps_run"]
 
-    for i in range(args.warmup):
-        wost.wost_solve_advance(job, args.iters, stream)
+    for _ in range(warmup):
+        wost.wost_solve_advance(job, iters, stream)
         stream.synchronize()
-    _log(f"warm-up done: {steps_run():.4e} steps run")
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    _barrier(world)
-    torch.cuda.synchronize()
-    total_steps = 0
-    dev_ms = 0.0
-    per_launch_ms = []
-    for i in range(args.steps):
+    total = 0
+    dev_ms = []
+    for i in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(i))  # evict the scene and the walk state from L2
         s0 = steps_run()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        wost.wost_solve_advance(job, args.iters, stream)
+        wost.wost_solve_advance(job, iters, stream)
         ev1.record(stream)
         ev1.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        dev_ms += ms
-        per_launch_ms.append(ms)
-        total_steps += steps_run() - s0
-    torch.cuda.synchronize()
-    _barrier(world)
-    clk = clocks.stop()
-    _, _, wd, pr = wost.wost_poll(job, n_all)
-    wost.wost_solve_destroy(job)
+        dev_ms.append(ev0.elapsed_time(ev1))
+        total += steps_run() - s0
+    return job, total, sum(dev_ms) * 1e-3, dev_ms
 
-    t_max = _max_over_ranks(dev_ms * 1e-3, world, "cuda")
-    steps_all = _sum_over_ranks(float(total_steps), world, "cuda")
-    value = steps_all / t_max
-    _log(f"timed {args.steps} launches: {value:.3e} steps/s ({dev_ms / args.steps:.0f} ms per launch)")
 
-    # end to end through the C ABI with host buffers: a whole solve of every
-    # e2e_batches-th grid point (host points in, host estimates out, the
-    # copies and the tail of the longest walks inside the timed region)
-    _barrier(world)
-    e2e_steps = 0
-    e2e_h2d = e2e_d2h = 0
-    t0 = time.perf_counter()
-    for i in range(args.e2e_steps):
-        pts_h = np.ascontiguousarray(grid_pts[i :: args.e2e_batches])
-        h = wost.wost_solve(S.handle, pts_h, walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
-                            seed=seed0 + 500 + i, kernel="resumable", block_size=args.block)
-        wost.wost_wait(h, 900.0)
-        mean, se, wdone, pe = wost.wost_poll(h, len(pts_h))
-        wost.wost_solve_destroy(h)
-        e2e_steps += pe["total_steps"]
-        steps_per_walk = pe["total_steps"] / max(1, int(wdone.sum()))
-        e2e_h2d += pts_h.nbytes
-        e2e_d2h += len(pts_h) * 8 * 4 + 4 * 8 + 16  # sum, sumsq, walks, steps + counters
-        u = scenes.exact_u("sin2x_cos3y", (), pts_h)
-        e2e_rel = float(np.sqrt(np.sum((mean - u) ** 2) / np.sum(u ** 2)))
-    e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
-    e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
-    _log(f"e2e {e2e_val:.3e} steps/s")
+def _rel_rms(mean, u):
+    return float(np.sqrt(np.sum((np.asarray(mean) - u) ** 2) / np.sum(u**2)))
 
-    peaks, peak_src = _measured_peaks()
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
-    fp32_peak = 2 * 128 * sms * mhz * 1e6  # FMA = 2 flops, 128 FP32 lanes per SM
-    l2_gbs = measure_l2_read_gbs(torch, stream)
-    kern_avg = dev_ms * 1e-3 / args.steps
-    steps_per_launch = total_steps / args.steps
-    achieved_b = bytes_step * steps_per_launch / kern_avg / 1e9
-    achieved_f = flops_step * steps_per_launch / kern_avg / 1e12
-    t_mem = bytes_step / (l2_gbs * 1e9)
-    t_alu = flops_step / fp32_peak
-    if t_mem >= t_alu:
-        roof = {"bound": "l2", "achieved": achieved_b, "peak": l2_gbs, "unit": "GB/s", "frac": achieved_b / l2_gbs,
-                "traffic": None}
-    else:
-        roof = {"bound": "alu", "achieved": achieved_f, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved_f / (fp32_peak / 1e12), "traffic": None}
-    roof.update({
-        "kernel": "k_walk_resume<2>", "unit_of_work": "walk step",
-        "bytes_per_step": bytes_step, "flops_per_step": flops_step,
-        "l2_frac": achieved_b / l2_gbs, "l2_peak_gbs": l2_gbs, "l2_peak_src": "measured in this run (64 MiB resident read)",
-        "fp32_frac": achieved_f / (fp32_peak / 1e12), "fp32_peak_tflops": fp32_peak / 1e12,
-        "fp32_peak_src": f"2 x 128 x {sms} SMs x {mhz:.0f} MHz (median SM clock of the run)",
-        "hbm_frac": achieved_b / peaks["hbm_gbs"], "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_src": peak_src,
-        "kernel_ms_avg": 1e3 * kern_avg, "counts_per_step": {k: v / r["total_steps"] for k, v in r["counts"].items()},
-    })
-    if rank == 0:
-        _log("oracle CPU baseline")
-        base = cpu_baseline(sc, walks=args.cpu_walks) if (world == 1 and not args.no_cpu) else None
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config_block(sc, {"kernel": "resumable", "block": args.block or 128,
-                                         "parallelism": f"replicas x{world}",
-                                         "step": f"one launch of the whole-grid job ({n_all} points x {walks} walks):"
-                                                 f" every resident lane runs up to {args.iters} walk steps, drawing"
-                                                 f" new walks and carrying unfinished ones to the next launch",
-                                         "iters_per_launch": args.iters}),
-            "points_per_s": value / (steps_per_walk * walks),
-            "mean_steps_per_walk": steps_per_walk,
-            "launch_ms": per_launch_ms,
-            "job_progress": {"walks_done": int(pr["walks_done"]), "steps_run": int(pr["steps_run"]),
-                             "launches": int(pr["launches"])},
-            "e2e": {"value": e2e_val, "unit": UNIT,
-                    "h2d_bytes_per_step": int(e2e_h2d / max(args.e2e_steps, 1)),
-                    "d2h_bytes_per_step": int(e2e_d2h / max(args.e2e_steps, 1)),
-                    "what": f"complete resumable solves of every {args.e2e_batches}th grid point x {walks} walks from"
-                            f" host memory (wost_solve + wost_wait + wost_poll), per solve",
-                    "rel_rms_error_vs_exact": e2e_rel},
-            "gpu_launches": args.steps,
-            "clocks": clk,
-            "roofline": roof,
-            "cpu_baseline": base,
-            "scene": {k: info[k] for k in ("n_dirichlet", "n_neumann", "n_silhouette", "nodes_dirichlet",
-                                           "nodes_neumann", "nodes_silhouette", "depth_dirichlet",
-                                           "depth_neumann", "depth_silhouette", "device_bytes", "build_seconds",
-                                           "lanes_per_walk")},
-        }
-        print(json.dumps(line), flush=True)
+
+def error_condition(steps_per_s, steps_per_walk, walks, rel_rms, target=0.01):
+    """Walks per point for `target` relative RMS error and points/s there,
+    from an error measured at `walks` walks: the error of a mean of
+    independent walks falls as walks^-1/2 (the epsilon-shell bias, below
+    1e-3 relative here, is neglected)."""
+    need = walks * (rel_rms / target) ** 2
+    return {"target_rel_rms": target, "measured_rel_rms": rel_rms, "at_walks_per_point": walks,
+            "walks_per_point_needed": need, "points_per_s_at_target": steps_per_s / (need * steps_per_walk),
+            "model": "rel RMS ~ walks^-1/2 from the measured point"}
+
+
+def sub_flower(wost, torch, stream):
+    """Workload 1: the 64-segment flower, 256 points x 512 walks, one launch
+    of the plain and of the persistent kernel (device time), RMS against
+    the exact solution."""
+    from paper_2302_11815_gb300 import scenes
+
+    sc = scenes.config1()
+    S = wost.Scene(sc)
+    pts = torch.from_numpy(sc["points"]).cuda()
+    u = scenes.exact_u("exp_cos", (), sc["points"])
+    out = {"workload": "flower64_laplace_2d_256pts_w512", "points": len(pts), "walks_per_point": sc["walks"]}
+    for kernel in ("plain", "persistent"):
+        best = None
+        for rep in range(3):
+            r = wost.solve(S, pts, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=17 + rep,
+                           kernel=kernel, stream=stream)
+            if best is None or r["elapsed_seconds"] < best["elapsed_seconds"]:
+                best = r
+        out[kernel] = {"seconds": best["elapsed_seconds"], "walk_steps_per_s": best["total_steps"] / best["elapsed_seconds"],
+                       "points_per_s": len(pts) / best["elapsed_seconds"], "rel_rms_vs_exact": _rel_rms(best["mean"], u),
+                       "steps": int(best["total_steps"]), "capped_walks": int(best["capped_walks"])}
     S.close()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.destroy_process_group()
-    return 0
+    return out
 
 
-def run_batch(args):
-    """Workload 4: many scenes in one batched persistent launch against one
-    launch per scene (persistent and plain kernels).  The three forms run the
-    same walks (same seeds), so their RMS errors are equal by construction;
-    the line reports their times."""
-    import torch
+def sub_cube_torus(wost, torch, args, stream, flush, peaks, peak_src, l2_gbs, hbm_gbs, fp32, fp32_src):
+    """Workload 3: cube around a noisy 200k-triangle torus, ~850k slice points
+    x 128 walks.  Timed like the headline (resumable launches of the whole
+    job), with its own work model and roofline; the RMS error against the
+    exact solution from a complete solve of a seeded subsample."""
+    from paper_2302_11815_gb300 import scenes
 
-    from paper_2302_11815_gb300 import scenes, wost
+    sc = scenes.config3()
+    S = wost.Scene(sc)
+    info = S.info()
+    pts = np.ascontiguousarray(sc["points"], np.float32)
+    rng = np.random.default_rng(3)
+    sub = pts[rng.choice(len(pts), 4096, replace=False)]
+    r = wost.solve(S, torch.from_numpy(sub[:512]).cuda(), 32, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=3,
+                   kernel="counting")
+    b_step, f_step = work_per_step(r["counts"], r["total_steps"], 3, info)
+    pts_dev = torch.from_numpy(pts).cuda()
+    job, steps, secs, ms = _resumable_launches(wost, torch, S, pts_dev, sc, stream, flush, args.iters3, 2,
+                                               args.steps3, seed=31)
+    wost.wost_solve_destroy(job)
+    full = wost.solve(S, torch.from_numpy(sub).cuda(), sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"],
+                      seed=33, kernel="resumable", stream=stream)
+    u = scenes.exact_u("quad3", (), sub)
+    spw = full["total_steps"] / max(1, int(full["walks"].sum()))
+    rate = steps / secs
+    rel = _rel_rms(full["mean"], u)
+    roof = roofline_block("k_walk_resume<3>", b_step, f_step, steps, secs, args.steps3, peaks, peak_src, l2_gbs,
+                          hbm_gbs, fp32, fp32_src, profiled_traffic("k_walk_resume<3>", kernel_source_hash()),
+                          {k: v / r["total_steps"] for k, v in r["counts"].items()})
+    out = {"workload": "cube_torus200k_laplace_3d_slices578_w128", "points": len(pts), "walks_per_point": sc["walks"],
+           "prims": int(len(sc["prims"])), "walk_steps_per_s": rate, "launches": args.steps3,
+           "iters_per_launch": args.iters3, "launch_ms": ms, "mean_steps_per_walk": spw,
+           "points_per_s": rate / (spw * sc["walks"]),
+           "rel_rms_vs_exact": rel, "rms_sample": f"{len(sub)} seeded points x {sc['walks']} walks, complete solve",
+           "capped_walks": int(full["capped_walks"]), "roofline": roof,
+           "error_condition": error_condition(rate, spw, sc["walks"], rel)}
+    S.close()
+    return out
 
-    wost.load()
+
+def sub_batch(wost, torch, args):
+    """Workload 4: many scenes in one batched persistent launch per dimension
+    against one launch per scene (persistent and plain kernels).  The three
+    forms run the same walks (same seeds), so their RMS errors are equal by
+    construction (checked: the largest relative difference of the means)."""
+    from paper_2302_11815_gb300 import scenes
+
     t0 = time.perf_counter()
     specs = scenes.config4(n_scenes=args.batch_scenes, points=(1, args.batch_max_points),
                            walks=(16, args.batch_max_walks), max_scene=args.batch_max_prims)
@@ -469,7 +482,6 @@ def run_batch(args):
         b.synchronize()
         return res, a.elapsed_time(b) * 1e-3
 
-    batched()  # warm-up
     rb, tb = timed(batched)
     rp, tp = timed(lambda: per_scene("persistent"))
     rq, tq = timed(lambda: per_scene("plain"))
@@ -480,46 +492,45 @@ def run_batch(args):
     for r, sc in zip(rb, specs):
         u = scenes.exact_u(*sc["exact"], sc["points"])
         err2 += float(np.sum((r[0] - u) ** 2))
-        ref2 += float(np.sum(u ** 2))
-    line = {"mode": "batch", "metric": "walk_steps_per_s", "unit": UNIT, "n_scenes": len(specs),
-            "dims": [s["dim"] for s in specs], "total_walks": int(walks), "total_steps": int(steps),
-            "total_points": int(sum(len(s["points"]) for s in specs)),
-            "batched": {"seconds": tb, "value": steps / tb, "launches": len({s["dim"] for s in specs})},
-            "per_scene_persistent": {"seconds": tp, "value": steps / tp, "launches": len(specs)},
-            "per_scene_plain": {"seconds": tq, "value": steps / tq, "launches": len(specs)},
-            "speedup_vs_plain": tq / tb, "rel_rms_error_all_forms": float(np.sqrt(err2 / ref2)),
-            "max_rel_diff_batched_vs_plain": maxdiff, "generation_seconds": gen_s,
-            "config": {"workload": "batched_64_scenes", "points_max": args.batch_max_points,
-                       "walks_max": args.batch_max_walks, "prims_max": args.batch_max_prims}}
-    print(json.dumps(line), flush=True)
+        ref2 += float(np.sum(u**2))
     for s in S:
         s.close()
-    return 0
+    return {"workload": f"batched_{len(specs)}_scenes", "n_scenes": len(specs),
+            "scenes_2d": sum(1 for s in specs if s["dim"] == 2), "total_walks": int(walks), "total_steps": int(steps),
+            "total_points": int(sum(len(s["points"]) for s in specs)),
+            "total_prims": int(sum(len(s["prims"]) for s in specs)),
+            "batched": {"seconds": tb, "walk_steps_per_s": steps / tb, "launches": len({s["dim"] for s in specs})},
+            "per_scene_persistent": {"seconds": tp, "walk_steps_per_s": steps / tp, "launches": len(specs)},
+            "per_scene_plain": {"seconds": tq, "walk_steps_per_s": steps / tq, "launches": len(specs)},
+            "speedup_vs_plain": tq / tb, "speedup_vs_per_scene_persistent": tp / tb,
+            "rel_rms_error_all_forms": float(np.sqrt(err2 / ref2)), "max_rel_diff_batched_vs_plain": maxdiff,
+            "generation_seconds": gen_s,
+            "sizes": {"points": [1, args.batch_max_points], "walks": [16, args.batch_max_walks],
+                      "prims": [1e3, args.batch_max_prims]},
+            "note": "same walks in all three forms (keyed random streams), so equal RMS error by construction"}
 
 
-def run_serve(args):
-    """Workload 5: resident 3D scenes, Poisson request stream into the
-    serving engine (continuous batching), latency percentiles and served
-    load."""
+def sub_serve(wost, torch, args):
+    """Workload 5: 8 resident 3D scenes (cube + noisy torus, ~5M triangles
+    together), a Poisson stream of requests into the serving engine
+    (continuous batching): p50/p99 latency of the completed requests, offered
+    against served load, rejections (memory budget, wait limit)."""
     import threading
 
-    import torch
+    from paper_2302_11815_gb300 import scenes
 
-    from paper_2302_11815_gb300 import scenes, wost
-
-    wost.load()
     t0 = time.perf_counter()
     specs = scenes.config5_scenes(total=args.serve_total_prims)
     S = [wost.Scene(s) for s in specs]
     reqs = scenes.config5_requests(duration_s=args.serve_seconds, rate=args.serve_rate,
                                    points=(1e3, args.serve_max_points))
     rng = np.random.default_rng(7)
-    pools = [[scenes.plane_points(rng, int(args.serve_max_points), s["tube"]) for _ in range(4)] for s in specs]
+    pools = [[scenes.plane_points(rng, int(args.serve_max_points), s["tube"]) for _ in range(2)] for s in specs]
     setup_s = time.perf_counter() - t0
-    eng = wost.wost_engine_create(round_seconds=args.round_seconds, max_walks_per_point=args.serve_walk_cap)
+    eng = wost.wost_engine_create(round_seconds=args.round_seconds, max_walks_per_point=args.serve_walk_cap,
+                                  max_wait_seconds=args.serve_max_wait)
     lock = threading.Lock()
-    live = []
-    done = []
+    live, done = [], []
     stop = threading.Event()
 
     def collector():
@@ -530,19 +541,19 @@ def run_serve(args):
                 h, rq, t_sub = item
                 try:
                     wost.wost_wait(h, 0.0)
-                    ok = True
+                    status = "ok"
                 except wost.WostError as e:
-                    if e.status == wost.ERR_TIMEOUT:
+                    if e.status == wost.ERR_TIMEOUT and not wost.wost_poll(h, rq["n_points"])[3]["done"]:
                         continue
-                    ok = False
+                    status = wost.STATUS_NAMES[e.status]
                 m, se, wd, pr = wost.wost_poll(h, rq["n_points"])
                 wost.wost_solve_destroy(h)
                 with lock:
                     live.remove(item)
-                    done.append({"latency": pr["elapsed_seconds"], "ok": ok, "n": rq["n_points"],
+                    done.append({"latency": pr["elapsed_seconds"], "status": status, "n": rq["n_points"],
                                  "walks": int(wd.min()), "se_max": float(se.max()), "target": rq["target_se"],
                                  "steps": pr["total_steps"]})
-            time.sleep(0.001)
+            time.sleep(0.002)
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
@@ -552,8 +563,7 @@ def run_serve(args):
         wait = rq["t"] - (time.perf_counter() - start)
         if wait > 0:
             time.sleep(wait)
-        pool = pools[rq["scene"]][rq["seed"] % 4]
-        pts = pool[: rq["n_points"]]
+        pts = pools[rq["scene"]][rq["seed"] % 2][: rq["n_points"]]
         sc = specs[rq["scene"]]
         h = wost.wost_engine_submit(eng, S[rq["scene"]].handle, pts, rq["target_se"], 0, sc["epsilon"],
                                     sc["r_min"], sc["max_steps"], seed=rq["seed"])
@@ -575,23 +585,196 @@ def run_serve(args):
     stats = wost.wost_engine_get_stats(eng)
     wost.wost_engine_destroy(eng)
     total = time.perf_counter() - start
-    ok = [d for d in done if d["ok"]]
+    ok = [d for d in done if d["status"] == "ok"]
     lat = np.array([d["latency"] for d in ok]) if ok else np.array([np.nan])
-    line = {"mode": "serve", "metric": "p99_latency_s", "unit": "s", "higher_is_better": False,
-            "p50_latency_s": float(np.nanpercentile(lat, 50)), "p99_latency_s": float(np.nanpercentile(lat, 99)),
-            "offered_requests": offered, "offered_rate": offered / max(window, 1e-9), "completed": len(ok),
-            "cancelled_at_end": len(done) - len(ok),
-            "served_points_per_s": sum(d["n"] for d in ok) / total,
-            "served_walk_steps_per_s": sum(d["steps"] for d in ok) / total,
-            "met_target": sum(1 for d in ok if d["se_max"] <= d["target"] * (1 + 1e-6)),
-            "capped": int(stats["capped"]), "engine": stats, "window_s": window, "total_s": total,
-            "setup_s": setup_s,
-            "config": {"workload": "serve_8_scenes", "scene_prims": [int(len(s["prims"])) for s in specs],
-                       "rate": args.serve_rate, "seconds": args.serve_seconds,
-                       "max_points": args.serve_max_points, "walk_cap": args.serve_walk_cap}}
-    print(json.dumps(line), flush=True)
     for s in S:
         s.close()
+    return {"workload": "serve_8_scenes_3d", "metric": "p99_latency_s",
+            "p50_latency_s": float(np.nanpercentile(lat, 50)) if ok else None,
+            "p99_latency_s": float(np.nanpercentile(lat, 99)) if ok else None,
+            "offered_requests": offered, "offered_rate_per_s": offered / max(window, 1e-9),
+            "completed": len(ok), "served_rate_per_s": len(ok) / total,
+            "rejected_wait_limit": sum(1 for d in done if d["status"] == "TIMEOUT"),
+            "cancelled_at_end": sum(1 for d in done if d["status"] == "CANCELLED"),
+            "met_target": sum(1 for d in ok if d["se_max"] <= d["target"] * (1 + 1e-6)),
+            "reached_walk_cap": int(stats["capped"]),
+            "served_points_per_s": sum(d["n"] for d in ok) / total,
+            "served_walk_steps_per_s": sum(d["steps"] for d in ok) / total,
+            "engine": stats, "window_s": window, "total_s": total, "setup_s": setup_s,
+            "scene_prims": [int(len(s["prims"])) for s in specs],
+            "config": {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                       "points": [1e3, args.serve_max_points], "walk_cap": args.serve_walk_cap,
+                       "max_wait_s": args.serve_max_wait, "drain_s": args.serve_drain,
+                       "targets": "SE 1e-2 or 1e-3, p = 1/2"}}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = _dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_2302_11815_gb300 import scenes, wost
+
+    wost.load()  # fails loudly when the CUDA library is missing
+    sc = scenes.config2()
+    grid_pts = np.ascontiguousarray(sc["points"], np.float32)
+    walks = sc["walks"]
+    S = wost.Scene(sc, device=local)
+    info = S.info()
+    _log(f"scene built: {info['n_dirichlet']} D + {info['n_neumann']} N prims, {len(grid_pts)} grid points")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    seed0 = 1000 * (rank + 1)
+
+    # work counts per step from the counting kernel on a subsample (untimed)
+    sub = torch.from_numpy(grid_pts[:: args.count_stride * 64].copy()).cuda()
+    r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting",
+                   timeout=600.0)
+    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2, info)
+    _log(f"work model: {r['total_steps']} steps counted, {bytes_step:.0f} B and {flops_step:.0f} flop per step")
+
+    # The job: every grid point x 256 walks (36 million walks, ~1.1e11 walk
+    # steps), device-resident, run as a resumable solve.  A bench step is
+    # one launch of it: every resident lane runs up to `iters` walk steps,
+    # drawing new walks as its walks end and carrying unfinished ones over.
+    pts_dev = torch.from_numpy(grid_pts).cuda()
+    n_all = len(grid_pts)
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    job, total_steps, dev_s, per_launch_ms = _resumable_launches(wost, torch, S, pts_dev, sc, stream, flush,
+                                                                 args.iters, args.warmup, args.steps, seed0,
+                                                                 block=args.block)
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+    _, _, wd, pr = wost.wost_poll(job, n_all)
+    wost.wost_solve_destroy(job)
+
+    t_max = _max_over_ranks(dev_s, world, "cuda")
+    steps_all = _sum_over_ranks(float(total_steps), world, "cuda")
+    value = steps_all / t_max
+    _log(f"timed {args.steps} launches: {value:.3e} steps/s ({1e3 * dev_s / args.steps:.0f} ms per launch)")
+
+    # end to end through the C ABI with host buffers: a whole solve of every
+    # e2e_batches-th grid point (host points in, host estimates out, the
+    # copies and the tail of the longest walks inside the timed region)
+    _barrier(world)
+    e2e_steps = 0
+    e2e_h2d = e2e_d2h = 0
+    e2e_err2 = e2e_ref2 = 0.0
+    e2e_walks = 0
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        pts_h = np.ascontiguousarray(grid_pts[i:: args.e2e_batches])
+        h = wost.wost_solve(S.handle, pts_h, walks, sc["epsilon"], sc["r_min"], sc["max_steps"],
+                            seed=seed0 + 500 + i, kernel="resumable", block_size=args.block)
+        wost.wost_wait(h, 900.0)
+        mean, se, wdone, pe = wost.wost_poll(h, len(pts_h))
+        wost.wost_solve_destroy(h)
+        e2e_steps += pe["total_steps"]
+        e2e_walks += int(wdone.sum())
+        e2e_h2d += pts_h.nbytes
+        e2e_d2h += len(pts_h) * 8 * 4 + 4 * 8 + 16  # sum, sumsq, walks, steps + counters
+        u = scenes.exact_u("sin2x_cos3y", (), pts_h)
+        e2e_err2 += float(np.sum((mean - u) ** 2))
+        e2e_ref2 += float(np.sum(u**2))
+    e2e_t = _max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e_val = _sum_over_ranks(float(e2e_steps), world, "cuda") / e2e_t
+    steps_per_walk = e2e_steps / max(1, e2e_walks)
+    e2e_rel = float(np.sqrt(e2e_err2 / e2e_ref2))
+    _log(f"e2e {e2e_val:.3e} steps/s, rel RMS {e2e_rel:.3f}")
+
+    peaks, peak_src = _measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1470.0)
+    fp32 = 2 * 128 * sms * mhz * 1e6 / 1e12  # TFLOP/s: FMA = 2 flops, 128 FP32 lanes per SM
+    fp32_src = f"2 x 128 x {sms} SMs x {mhz:.0f} MHz (median SM clock of the run)"
+    l2_gbs = measure_read_gbs(torch, wost, stream, 48 << 20, 40)
+    hbm_gbs = measure_read_gbs(torch, wost, stream, 4 << 30, 2, reps=3)
+    _log(f"read probe: L2 {l2_gbs:.0f} GB/s, HBM {hbm_gbs:.0f} GB/s")
+    roof = roofline_block("k_walk_resume<2>", bytes_step, flops_step, total_steps, dev_s, args.steps, peaks,
+                          peak_src, l2_gbs, hbm_gbs, fp32, fp32_src,
+                          profiled_traffic("k_walk_resume<2>", kernel_source_hash()),
+                          {k: v / r["total_steps"] for k, v in r["counts"].items()})
+    line_extra = {}
+    if rank == 0 and world == 1 and not args.headline_only:
+        for name, fn in (("flower", lambda: sub_flower(wost, torch, stream)),
+                         ("cube_torus_3d", lambda: sub_cube_torus(wost, torch, args, stream, flush, peaks, peak_src,
+                                                                  l2_gbs, hbm_gbs, fp32, fp32_src)),
+                         ("batch", lambda: sub_batch(wost, torch, args)),
+                         ("serve", lambda: sub_serve(wost, torch, args))):
+            _log(f"workload {name}")
+            try:
+                line_extra[name] = fn()
+            except Exception as ex:  # a failed extra workload must not hide the headline line
+                line_extra[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            _log(f"workload {name} done")
+    if rank == 0:
+        _log("oracle CPU baseline")
+        base = cpu_baseline(sc, walks=args.cpu_walks) if (world == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config_block(sc, {"kernel": "resumable", "block": args.block or 128,
+                                         "parallelism": f"replicas x{world}",
+                                         "step": f"one launch of the whole-grid job ({n_all} points x {walks} walks):"
+                                                 f" every resident lane runs up to {args.iters} walk steps, drawing"
+                                                 f" new walks and carrying unfinished ones to the next launch",
+                                         "iters_per_launch": args.iters}),
+            "points_per_s": value / (steps_per_walk * walks),
+            "mean_steps_per_walk": steps_per_walk,
+            "launch_ms": per_launch_ms,
+            "job_progress": {"walks_done": int(pr["walks_done"]), "steps_run": int(pr["steps_run"]),
+                             "launches": int(pr["launches"])},
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(e2e_h2d / max(args.e2e_steps, 1)),
+                    "d2h_bytes_per_step": int(e2e_d2h / max(args.e2e_steps, 1)),
+                    "what": f"complete resumable solves of every {args.e2e_batches}th grid point x {walks} walks from"
+                            f" host memory (wost_solve + wost_wait + wost_poll), per solve",
+                    "rel_rms_error_vs_exact": e2e_rel,
+                    "rel_rms_points": int(sum(len(grid_pts[i:: args.e2e_batches]) for i in range(args.e2e_steps)))},
+            "error_condition": error_condition(value, steps_per_walk, walks, e2e_rel),
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "roofline": roof,
+            "cpu_baseline": base,
+            "scene": {k: info[k] for k in ("n_dirichlet", "n_neumann", "n_silhouette", "nodes_dirichlet",
+                                           "nodes_neumann", "nodes_silhouette", "depth_dirichlet",
+                                           "depth_neumann", "depth_silhouette", "device_bytes", "build_seconds",
+                                           "lanes_per_walk", "stack_depth")},
+        }
+        line.update(line_extra)
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args):
+    """The batched workload alone (--mode batch)."""
+    import torch
+
+    from paper_2302_11815_gb300 import wost
+
+    wost.load()
+    print(json.dumps(dict(mode="batch", **sub_batch(wost, torch, args))), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """The serving workload alone (--mode serve)."""
+    import torch
+
+    from paper_2302_11815_gb300 import wost
+
+    wost.load()
+    print(json.dumps(dict(mode="serve", **sub_serve(wost, torch, args))), flush=True)
     return 0
 
 
@@ -627,15 +810,19 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--mode", default="main", choices=["main", "batch", "serve", "profile"])
     ap.add_argument("--batch-scenes", type=int, default=64)
-    ap.add_argument("--batch-max-points", type=float, default=1e5)
-    ap.add_argument("--batch-max-walks", type=float, default=1024)
-    ap.add_argument("--batch-max-prims", type=float, default=5e5)
+    ap.add_argument("--batch-max-points", type=float, default=5e3)
+    ap.add_argument("--batch-max-walks", type=float, default=128)
+    ap.add_argument("--batch-max-prims", type=float, default=1e5)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-max-points", type=float, default=2.56e5)
     ap.add_argument("--serve-total-prims", type=float, default=5e6)
-    ap.add_argument("--serve-walk-cap", type=int, default=65536)
+    ap.add_argument("--serve-walk-cap", type=int, default=4096)
+    ap.add_argument("--serve-max-wait", type=float, default=5.0)
     ap.add_argument("--serve-drain", type=float, default=30.0)
+    ap.add_argument("--iters3", type=int, default=1024, help="walk steps per lane per launch, 3D workload")
+    ap.add_argument("--steps3", type=int, default=5, help="timed launches, 3D workload")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")
     ap.add_argument("--round-seconds", type=float, default=0.02)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define WOST_ABI_VERSION 2
+#define WOST_ABI_VERSION 3
 
 typedef enum {
     WOST_OK = 0,
@@ -100,16 +100,32 @@ typedef struct {
 /* ---------------------------------------------------------------------- */
 typedef struct wost_scene wost_scene;
 
+/* Double-sided boundaries (App. B): a primitive flagged 2 or 3 bounds the
+ * domain on both of its sides (a crack, a thin sheet, an open surface).  Its
+ * canonical normal n+ is the outward normal above; the "+" side is the one
+ * n+ points away from (as for a one-sided primitive, whose domain lies
+ * behind its outward normal), the "-" side the one it points into.  g and h
+ * give the + side's data (h = du/dn+), g_minus and h_minus the - side's
+ * (h_minus = du/dn-, n- = -n+).  A walk uses the data of the side it is on:
+ * the side of x relative to the closest point (Dirichlet), the side it came
+ * from when it hits a Neumann sheet (its next direction stays on that side),
+ * and the side of the walk's query point relative to a Neumann sample.
+ * g_minus / h_minus may be NONE: then g- = g+ and h- = -h+ (a solution
+ * continuous across the sheet), which is also what analytic data give. */
 typedef struct {
     int32_t dim;               /* 2 or 3                                       */
     int64_t n_vertices;
     const float *vertices;     /* host [n_vertices * dim]                      */
     int64_t n_prims;
     const int32_t *prims;      /* host [n_prims * dim], indices < n_vertices   */
-    const uint8_t *flags;      /* host [n_prims]: 0 Dirichlet, 1 Neumann       */
+    const uint8_t *flags;      /* host [n_prims]: 0 Dirichlet, 1 Neumann,
+                                  2 double-sided Dirichlet, 3 double-sided
+                                  Neumann                                      */
     wost_field g, h, f;
     int32_t device;            /* CUDA device ordinal                          */
     int32_t leaf_size;         /* primitives per leaf, 0 = default (4)         */
+    wost_field g_minus, h_minus; /* - side data of double-sided primitives:
+                                  NONE, PER_VERTEX or PER_CORNER               */
 } wost_scene_desc;
 
 typedef struct {
@@ -128,6 +144,8 @@ typedef struct {
     int32_t node_bytes, cone_bytes;
     int64_t wide_nodes_dirichlet, wide_nodes_neumann, wide_nodes_silhouette;
     int32_t wide_depth_dirichlet, wide_depth_neumann, wide_depth_silhouette;
+    int32_t device;            /* CUDA device ordinal the scene lives on       */
+    int32_t stack_depth;       /* traversal stack entries per walk it needs    */
 } wost_scene_info;
 
 /* Builds the hierarchies on the host, uploads them, returns a handle.
@@ -194,6 +212,16 @@ typedef struct {
                                   Neumann problems (0 = every step).  Screened
                                   steps end walks by Russian roulette with
                                   the step weight Q of App. A.2              */
+    int32_t stack_depth;       /* traversal stack entries per walk, 0 = the
+                                  scene's (wost_scene_info.stack_depth, which
+                                  no traversal exceeds).  A smaller value saves
+                                  shared memory but a traversal that needs more
+                                  drops subtrees and sets guard bit 1, making
+                                  wost_wait / wost_poll return INTERNAL       */
+    int32_t visit_limit;       /* node visits allowed per traversal, 0 = twice
+                                  the tree's nodes plus 8 (more than a correct
+                                  traversal makes).  A traversal that reaches
+                                  the limit stops and sets guard bit 2        */
 } wost_solve_desc;
 
 typedef struct {
@@ -214,7 +242,8 @@ typedef struct {
  * The caller's arrays are copied before return.  Errors: INVALID_ARG
  * (n_points < 1, walks < 1, epsilon <= 0, r_min > epsilon, max_steps < 1,
  * a null points array, sigma < 0 or not finite, screen_after < 0, sigma = 0
- * on a scene without Dirichlet primitives), OUT_OF_MEMORY, CUDA. */
+ * on a scene without Dirichlet primitives, stack_depth or visit_limit < 0),
+ * OUT_OF_MEMORY, CUDA. */
 wost_status wost_solve(wost_scene *scene, const wost_solve_desc *desc, wost_solve_handle **out);
 
 /* Resumable solves (desc->kernel = WOST_KERNEL_RESUMABLE): wost_solve
@@ -290,10 +319,10 @@ wost_status wost_screened_kernels(int32_t dim, int64_t n, const float *rho, cons
 /* For callers that cannot allocate device memory while they solve (a loop
  * that must not stall on the device synchronisation of cudaMalloc/cudaFree,
  * a process whose device memory is committed under a fixed budget).
- * Enqueues on `stream` (NULL = the legacy default stream) the walks that
- * wost_solve runs with WOST_KERNEL_PERSISTENT for the same arguments
- * (n_points x walks_per_point walks of Alg. 1, walk indices first_walk..,
- * Philox key seed) and writes the per-point mean to mean_out and, when
+ * Enqueues on `stream` (NULL = the legacy default stream) the n_points x
+ * walks_per_point walks that wost_solve runs with WOST_KERNEL_PERSISTENT for
+ * the same arguments (walk indices first_walk.., Philox key seed) and
+ * writes the per-point mean to mean_out and, when
  * stderr_out is not NULL, its standard error sqrt(sample variance / walks).
  * points (device, n_points * dim floats; interior points: no Neumann
  * normals), mean_out and stderr_out (device, n_points floats) belong to the
@@ -305,8 +334,9 @@ wost_status wost_screened_kernels(int32_t dim, int64_t n, const float *rho, cons
  *   - n_points > WOST_STATIC_MAX_POINTS is rejected with INVALID_ARG;
  *   - calls whose work overlaps on one device (other streams or threads)
  *     share that array and give wrong results: order them;
- *   - the first call on a device looks up the array's device address, which
- *     may load the module: make it before any stream capture.
+ *   - every call looks up the array's device address (a device reset or a
+ *     recreated context moves it); the first lookup on a device may load the
+ *     module: make the first call before any stream capture.
  * If a device guard fires (traversal stack overflow or visit limit), every
  * output is NaN.  Returns once the work is enqueued.  Errors: INVALID_ARG
  * (null scene, points or mean_out; n_points < 1 or above the maximum;
@@ -322,9 +352,12 @@ wost_status wost_solve_static(wost_scene *scene, int64_t n_points, const float *
  * in a FIFO until their state (points and FP64 accumulators) fits the
  * engine's device-memory budget, then join the running mix: every
  * scheduling round is one batched persistent launch over pieces (point
- * ranges x walk ranges) of all active requests, sized to about
- * round_seconds of GPU time, with up to two rounds queued so the GPU never
- * waits for the host.  A request runs in stages of walks per point
+ * ranges x walk ranges) of the active requests, sized to about
+ * round_seconds of GPU time but never so small that the resident grid runs
+ * short of walks; the round's walk-step budget goes to the active requests
+ * oldest first, so under overload the oldest complete first and the rest
+ * wait (or are shed by max_wait_seconds).  Up to two rounds are queued so
+ * the GPU never waits for the host.  A request runs in stages of walks per point
  * (min_walks, then growing from its own variance estimate); after each
  * stage it completes if its largest per-point standard error is at most its
  * target, or if it reached its walk cap.  A request's walks use its own
@@ -340,6 +373,9 @@ typedef struct {
     int32_t min_walks;            /* walks per point of the first stage; 0 = 16           */
     int32_t max_walks_per_point;  /* default walk cap; 0 = 65536                           */
     int32_t block_size;           /* threads per block; 0 = 128                            */
+    double max_wait_seconds;      /* a request whose first walks have not started this long
+                                     after submission is finished with TIMEOUT and counted
+                                     as rejected (overload shedding); 0 = wait forever    */
 } wost_engine_desc;
 
 typedef struct {
@@ -418,6 +454,20 @@ typedef struct {
  * launches whose block_size is 0.  Same validation as wost_solve. */
 wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t n, int32_t walks_per_point,
                                 float epsilon, float r_min, int32_t max_steps, wost_tune_result *out);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement helper (no counterpart in the paper)                        */
+/* ---------------------------------------------------------------------- */
+/* Enqueues on `stream` one read sweep kernel over the caller's device buffer
+ * (bytes, 16-byte aligned, a multiple of 16): `passes` sweeps of 16-byte
+ * loads that bypass L1, resident grid.  It measures the read bandwidth of
+ * the level the buffer lives in -- L2 for a buffer well below the L2 size,
+ * HBM for one well above it -- for the roofline of the walk kernels, whose
+ * scene data are L2-resident.  The caller times it (CUDA events on
+ * `stream`); sink (device, 1 float) receives a value only in a case that
+ * cannot occur with finite data.  Allocates nothing.  Errors: INVALID_ARG,
+ * CUDA. */
+wost_status wost_read_probe(const void *buf, int64_t bytes, int32_t passes, float *sink, void *stream);
 
 /* Thread-local description of the last failure on this thread. */
 const char *wost_last_error(void);

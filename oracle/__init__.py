@@ -33,6 +33,8 @@ Boundary data and analytic solutions, and the pins that exercise each:
   data per_vertex   linear u on a square (2D) and on a cube with a Neumann
                     face (3D): exact; equal to per-corner walk for walk
   data grid         screened source on a grid (bilinear, clamped)
+  double-sided      (App. B) slit square with g+ != g- (u = polar angle),
+                    Neumann sheets inside a Dirichlet box (2D, 3D)
   fn zero           Poisson kernel of the disk
   fn exp_cos        pure Dirichlet disk, the 64-segment flower, convergence
   fn sin2x_cos3y    f = 13 u on a Dirichlet disk and with a Neumann half
@@ -100,6 +102,7 @@ def _L():
             lib.orc_scene_new.restype = P
             lib.orc_scene_new.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, P, P, P]
             lib.orc_scene_free.argtypes = [P]
+            lib.orc_scene_set_minus.argtypes = [P, P, P]
             lib.orc_scene_info.argtypes = [P, P]
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_closest_dirichlet.argtypes = [P, C.c_int64, P, P, P, P]
@@ -180,6 +183,9 @@ class Scene:
                                     _ptr(Pm), _ptr(Fl), C.byref(g), C.byref(h), C.byref(f))
         if not self._h:
             raise ValueError("oracle rejected the scene")
+        if "g_minus" in spec or "h_minus" in spec:
+            gm, hm = (_field(spec.get(k), keep) for k in ("g_minus", "h_minus"))
+            lib.orc_scene_set_minus(self._h, C.byref(gm), C.byref(hm))
 
     def info(self):
         out = np.zeros(8, np.int64)

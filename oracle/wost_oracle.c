@@ -309,6 +309,10 @@ struct orc_scene {
     int32_t *tprims;
     orc_field g, h, f;
     double *gv, *hv, *fv;
+    /* App. B: data of the - side of double-sided primitives (flags 2, 3);
+     * kind NONE: g- = g+, h- = -h+ */
+    orc_field gm, hm;
+    double *gmv, *hmv;
     double blo[3], bhi[3]; /* R13: grown bounding box of the vertices */
     double rmax;           /* R14: diagonal of the vertices' bounding box */
 };
@@ -433,8 +437,8 @@ orc_scene *orc_scene_new(int dim, int nv, const double *vertices, int np, const 
         s->area[p] = A;
         s->live[p] = A > 0;
         if (!s->live[p]) continue;
-        if (flags[p]) s->Nl[s->nN++] = p;
-        else s->Dl[s->nD++] = p;
+        if (flags[p] & 1) s->Nl[s->nN++] = p; /* 1, 3: Neumann (3 double-sided) */
+        else s->Dl[s->nD++] = p;            /* 0, 2: Dirichlet (2 double-sided) */
     }
     /* silhouette candidates */
     if (dim == 2) {
@@ -539,7 +543,19 @@ void orc_scene_free(orc_scene *s) {
     free(s->V); free(s->P); free(s->flags); free(s->live); free(s->nrm); free(s->area);
     free(s->Dl); free(s->Nl); free(s->sa); free(s->sb); free(s->snadj); free(s->sf0);
     free(s->sf1); free(s->nodes); free(s->tprims); free(s->gv); free(s->hv); free(s->fv);
+    free(s->gmv); free(s->hmv);
     free(s);
+}
+
+void orc_scene_set_minus(orc_scene *s, const orc_field *gm, const orc_field *hm) {
+    orc_field none;
+    memset(&none, 0, sizeof none);
+    free(s->gmv); free(s->hmv);
+    s->gm = gm ? *gm : none;
+    s->hm = hm ? *hm : none;
+    s->gmv = copy_vals(gm, field_len(s, gm));
+    s->hmv = copy_vals(hm, field_len(s, hm));
+    s->gm.values = s->gmv; s->hm.values = s->hmv;
 }
 
 int orc_scene_info(const orc_scene *s, int64_t *out) {
@@ -653,18 +669,30 @@ static double interp_prim(const orc_scene *s, const orc_field *fd, int p, const 
 static void bary_of(const orc_scene *s, int p, V3 q, double bary[3]) {
     closest_on_prim(s, p, q, bary);
 }
-static double eval_g(const orc_scene *s, int p, V3 q, const double bary[3]) {
+/* App. B: a double-sided primitive carries data for each of its sides */
+static int double_sided(const orc_scene *s, int p) { return s->flags[p] >= 2; }
+static double eval_g(const orc_scene *s, int p, V3 q, const double bary[3], int minus) {
+    if (minus && (s->gm.kind == ORC_DATA_PER_VERTEX || s->gm.kind == ORC_DATA_PER_CORNER))
+        return interp_prim(s, &s->gm, p, bary);
     if (s->g.kind == ORC_DATA_ANALYTIC) return fn_u(s->dim, s->g.fn, s->g.params, q);
     if (s->g.kind == ORC_DATA_PER_VERTEX || s->g.kind == ORC_DATA_PER_CORNER)
         return interp_prim(s, &s->g, p, bary);
     return 0.0;
 }
-static double eval_h(const orc_scene *s, int p, V3 q) {
-    if (s->h.kind == ORC_DATA_ANALYTIC) return dot(fn_grad(s->dim, s->h.fn, s->h.params, q), s->nrm[p]);
+/* h on the + side is du/dn+ (n+ the primitive's normal); on the - side
+ * du/dn- with n- = -n+: the given - side data, else -h+ */
+static double eval_h(const orc_scene *s, int p, V3 q, int minus) {
+    if (s->h.kind == ORC_DATA_ANALYTIC) {
+        double hp = dot(fn_grad(s->dim, s->h.fn, s->h.params, q), s->nrm[p]);
+        return minus ? -hp : hp;
+    }
+    double bary[3];
+    bary_of(s, p, q, bary);
+    if (minus && (s->hm.kind == ORC_DATA_PER_VERTEX || s->hm.kind == ORC_DATA_PER_CORNER))
+        return interp_prim(s, &s->hm, p, bary);
     if (s->h.kind == ORC_DATA_PER_VERTEX || s->h.kind == ORC_DATA_PER_CORNER) {
-        double bary[3];
-        bary_of(s, p, q, bary);
-        return interp_prim(s, &s->h, p, bary);
+        double hp = interp_prim(s, &s->h, p, bary);
+        return minus ? -hp : hp;
     }
     return 0.0;
 }
@@ -970,7 +998,10 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
             /* epsilon shell: return g at the closest point; R5, R13: same at
              * the cap and outside the grown bounding box */
             if (dD >= pr->epsilon) *capped_out = 1;
-            if (primD >= 0) acc += eval_g(s, primD, xbar, bary);
+            /* App. B: the - side's data when x lies on the side of a
+             * double-sided primitive that its normal n+ points into */
+            int minus = primD >= 0 && double_sided(s, primD) && !(dot(sub(xbar, x), s->nrm[primD]) > 0);
+            if (primD >= 0) acc += eval_g(s, primD, xbar, bary, minus);
             if (rows && *nrows < max_rows) {
                 double *row = rows + (size_t)(*nrows) * ORC_TRACE_COLS;
                 row[0] = x.x; row[1] = x.y; row[2] = x.z; row[3] = onN; row[4] = dD;
@@ -1004,6 +1035,9 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
         if (hit) {
             p = add(xq, scl(v, th));
             np = s->nrm[hprim];
+            /* App. B: at a double-sided sheet the walk stays on the side it
+             * came from: the outward normal there is the one it moves along */
+            if (double_sided(s, hprim) && dot(v, np) < 0) np = scl(np, -1.0);
         } else {
             p = add(x, scl(v, r));
         }
@@ -1025,7 +1059,11 @@ static double walk(const orc_scene *s, V3 x, V3 nx, int onN, uint32_t pidx, uint
                 if (!occluded) {
                     double alpha = onN ? 0.5 : 1.0;
                     double G = sig > 0 ? orc_screened_green_ball(dim, dz, r, sig) : orc_green_ball(dim, dz, r);
-                    Nterm = G * eval_h(s, zprim, z) / (alpha * pdf);
+                    /* App. B: the data of the side of a double-sided sheet
+                     * that faces the query point xq (which lies off the
+                     * boundary on the walk's side, R4) */
+                    int minus = double_sided(s, zprim) && !(dot(sub(z, xq), s->nrm[zprim]) > 0);
+                    Nterm = G * eval_h(s, zprim, z, minus) / (alpha * pdf);
                 }
             }
         }

@@ -67,6 +67,12 @@ orc_scene *orc_scene_new(int dim, int nv, const double *vertices, int np,
                          const orc_field *g, const orc_field *h,
                          const orc_field *f);
 void orc_scene_free(orc_scene *s);
+
+/* App. B: data of the - side of double-sided primitives (flags 2 =
+ * double-sided Dirichlet, 3 = double-sided Neumann).  NONE: g- = g+ and
+ * h- = -h+ (a solution continuous across the sheet).  The + side of a
+ * primitive is the one its normal n+ points away from. */
+void orc_scene_set_minus(orc_scene *s, const orc_field *gm, const orc_field *hm);
 int orc_scene_info(const orc_scene *s, int64_t *out /* [8] */);
 
 /* Philox4x32-10 (Salmon et al., SC'11), one block. */

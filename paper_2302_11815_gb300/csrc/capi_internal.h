@@ -72,6 +72,7 @@ struct wost_scene {
     wost::SceneView view{};
     wost::DevBuf bufs[16];
     wost::DevBuf wbufs[6];  // wide layout: nodes and cones of the three trees
+    wost::DevBuf sbufs[4];  // double-sided records (App. B): - side data and flags of D and N
     wost::DevBuf n_rec_of_id;
     unsigned int *guard = nullptr;        // device guard word for query kernels
     wost::SceneView *view_dev = nullptr;  // device copy of `view` (batched launches)

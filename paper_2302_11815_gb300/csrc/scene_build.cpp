@@ -381,7 +381,8 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
     for (int64_t i = 0; i < d.n_prims * dim; ++i)
         if (d.prims[i] < 0 || d.prims[i] >= d.n_vertices) return "primitive index out of range";
     for (int64_t i = 0; i < d.n_prims; ++i)
-        if (d.flags[i] > 1) return "flag must be 0 (Dirichlet) or 1 (Neumann)";
+        if (d.flags[i] > 3)
+            return "flag must be 0 (Dirichlet), 1 (Neumann), 2 or 3 (double-sided Dirichlet or Neumann)";
     auto check_field = [&](const wost_field &f, bool is_source) -> std::string {
         switch (f.kind) {
         case WOST_DATA_NONE: return "";
@@ -416,6 +417,11 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
     if (!(e = check_field(d.g, false)).empty()) return "g: " + e;
     if (!(e = check_field(d.h, false)).empty()) return "h: " + e;
     if (!(e = check_field(d.f, true)).empty()) return "f: " + e;
+    for (const wost_field *m : {&d.g_minus, &d.h_minus}) {
+        if (m->kind != WOST_DATA_NONE && m->kind != WOST_DATA_PER_VERTEX && m->kind != WOST_DATA_PER_CORNER)
+            return "g_minus / h_minus must be NONE, PER_VERTEX or PER_CORNER";
+        if (!(e = check_field(*m, false)).empty()) return (m == &d.g_minus ? "g_minus: " : "h_minus: ") + e;
+    }
 
     S.dim = dim;
     auto V = [&](int64_t v) -> V3 {
@@ -445,7 +451,7 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
             S.n_dropped++;
             continue;
         }
-        (d.flags[p] ? Nl : Dl).push_back(p);
+        (d.flags[p] & 1 ? Nl : Dl).push_back(p);
     }
 
     // scene bounds
@@ -484,14 +490,23 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
             for (int k = 0; k < dim; ++k) out[k] = f.values[p * dim + k];
     };
 
-    // primitive records of a D or N tree in leaf order
+    // primitive records of a D or N tree in leaf order; double-sided records
+    // (flags 2, 3) also get their - side corner data (NONE: the + side's data
+    // for g, negated for h, i.e. a solution continuous across the sheet)
     auto fill_prims = [&](const std::vector<int64_t> &list, const std::vector<int> &perm, const wost_field &fld,
-                          HostTree &t) {
+                          const wost_field &minus, bool negate_plus, HostTree &t) {
         size_t n = list.size();
         t.prims.assign(n * (dim == 2 ? 1 : 3), f4(0, 0, 0, 0));
         t.data.assign(dim == 2 ? (n + 1) / 2 : n, f4(0, 0, 0, 0));
         t.ids.resize(n);
+        bool any_sided = false;
+        for (int64_t p : list) any_sided = any_sided || d.flags[p] >= 2;
+        if (any_sided) {
+            t.sided.assign(n, 0);
+            t.data_minus.assign(t.data.size(), f4(0, 0, 0, 0));
+        }
         float *dat = reinterpret_cast<float *>(t.data.data());
+        float *datm = any_sided ? reinterpret_cast<float *>(t.data_minus.data()) : nullptr;
         for (size_t k = 0; k < n; ++k) {
             int64_t p = list[perm[k]];
             t.ids[k] = (int32_t)p;
@@ -506,13 +521,17 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
             }
             float cv[3];
             corner_vals(fld, p, cv);
-            if (dim == 2) {
-                dat[2 * k] = cv[0];
-                dat[2 * k + 1] = cv[1];
-            } else {
-                dat[4 * k] = cv[0];
-                dat[4 * k + 1] = cv[1];
-                dat[4 * k + 2] = cv[2];
+            const int stride = dim == 2 ? 2 : 4;
+            for (int c = 0; c < dim; ++c) dat[stride * k + c] = cv[c];
+            if (any_sided && d.flags[p] >= 2) {
+                t.sided[k] = 1;
+                float mv[3];
+                if (minus.kind == WOST_DATA_NONE) {
+                    for (int c = 0; c < 3; ++c) mv[c] = negate_plus ? -cv[c] : cv[c];
+                } else {
+                    corner_vals(minus, p, mv);
+                }
+                for (int c = 0; c < dim; ++c) datm[stride * k + c] = mv[c];
             }
         }
     };
@@ -522,14 +541,14 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
         std::vector<Item> items(Dl.size());
         for (size_t i = 0; i < Dl.size(); ++i) items[i] = prim_item(Dl[i], (int)i);
         auto perm = build_tree(items, dim, leaf, S.D, nullptr, nullptr);
-        fill_prims(Dl, perm, d.g, S.D);
+        fill_prims(Dl, perm, d.g, d.g_minus, false, S.D);
     }
     // --- Neumann BVH ---
     {
         std::vector<Item> items(Nl.size());
         for (size_t i = 0; i < Nl.size(); ++i) items[i] = prim_item(Nl[i], (int)i);
         auto perm = build_tree(items, dim, leaf, S.N, nullptr, nullptr);
-        fill_prims(Nl, perm, d.h, S.N);
+        fill_prims(Nl, perm, d.h, d.h_minus, true, S.N);
     }
     // --- silhouette candidates and their cone hierarchy ---
     struct Sil {

@@ -13,6 +13,8 @@ namespace wost {
 
 struct HostTree {
     std::vector<float4> nodes, cones, prims, data;
+    std::vector<float4> data_minus;  // - side corner data (double-sided records; empty if none)
+    std::vector<uint8_t> sided;      // per record: 1 = double-sided (empty if none is)
     std::vector<int32_t> ids;
     uint32_t root = WOST_EMPTY_REF;
     float root_lo[3] = {0, 0, 0}, root_hi[3] = {0, 0, 0};

@@ -92,6 +92,14 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
             V.wn_nodes = T.wn_nodes;
             V.wdepth = T.wdepth;
         }
+        for (int t = 0; t < 2; ++t) {  // double-sided records of D and N
+            HostTree &T = *trees[t];
+            CK(upload(s->sbufs[2 * t], T.data_minus), "upload data");
+            CK(upload(s->sbufs[2 * t + 1], T.sided), "upload flags");
+            bytes += (int64_t)(s->sbufs[2 * t].bytes + s->sbufs[2 * t + 1].bytes);
+            views[t]->data_minus = (const float4 *)s->sbufs[2 * t].p;
+            views[t]->sided = (const uint8_t *)s->sbufs[2 * t + 1].p;
+        }
         CK(upload(s->bufs[15], H.grid), "upload grid");
         bytes += (int64_t)s->bufs[15].bytes;
         std::vector<int32_t> rec_of_id((size_t)desc->n_prims, -1);
@@ -148,6 +156,8 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         I.wide_depth_silhouette = H.S.wdepth;
         I.device_bytes = bytes;
         I.build_seconds = H.build_seconds;
+        I.device = s->device;
+        I.stack_depth = s->stack_depth;
         for (int a = 0; a < 3; ++a) {
             I.bbox_lo[a] = H.lo[a];
             I.bbox_hi[a] = H.hi[a];
@@ -189,6 +199,12 @@ wost_status wost_scene_validate(const wost_scene_desc *desc, wost_scene_info *ou
         I.wide_depth_neumann = H.N.wdepth;
         I.wide_depth_silhouette = H.S.wdepth;
         I.build_seconds = H.build_seconds;
+        I.device = desc->device;
+#if WOST_TEAM == 1
+        I.stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
+#else
+        I.stack_depth = ((WOST_WIDE - 1) * std::max(H.D.wdepth, std::max(H.N.wdepth, H.S.wdepth)) + 1) | 1;
+#endif
         for (int a = 0; a < 3; ++a) {
             I.bbox_lo[a] = H.lo[a];
             I.bbox_hi[a] = H.hi[a];
@@ -231,6 +247,9 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     if (d->max_steps < 1) return fail(WOST_ERR_INVALID_ARG, "max_steps must be >= 1");
     if (!(d->sigma >= 0) || !std::isfinite(d->sigma)) return fail(WOST_ERR_INVALID_ARG, "sigma must be >= 0");
     if (d->screen_after < 0) return fail(WOST_ERR_INVALID_ARG, "screen_after must be >= 0");
+    if (d->stack_depth < 0 || d->stack_depth > 4096)
+        return fail(WOST_ERR_INVALID_ARG, "stack_depth must be 0 (the scene's) or 1..4096");
+    if (d->visit_limit < 0) return fail(WOST_ERR_INVALID_ARG, "visit_limit must be >= 0");
     if (scene->host.n_dirichlet == 0 && !(d->sigma > 0))
         return fail(WOST_ERR_INVALID_ARG, "a scene without Dirichlet primitives needs sigma > 0 (Tikhonov "
                                           "regularisation of the pure Neumann problem)");
@@ -293,7 +312,8 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     sp.key1 = (uint32_t)(d->seed >> 32);
     sp.offset = 1e-6f;
     sp.vis_tmax = 1.f - 1e-4f;
-    sp.stack_depth = scene->stack_depth;
+    sp.stack_depth = d->stack_depth ? d->stack_depth : scene->stack_depth;
+    sp.visit_limit = (uint32_t)d->visit_limit;
     sp.sigma = d->sigma;
     sp.sqrt_sigma = std::sqrt(d->sigma);
     sp.screen_after = d->screen_after;

@@ -126,6 +126,7 @@ struct Stack {
     int2 *base;
     int stride, cap;
     unsigned int *guard;
+    unsigned visit_limit;  // 0: 2 n_nodes + 8
 };
 __device__ __forceinline__ void spush(const Stack &s, int &sp, uint32_t ref, float key) {
     if (sp < s.cap) {
@@ -145,8 +146,10 @@ __device__ __forceinline__ void spop(const Stack &s, int &sp, uint32_t &ref, flo
 // A traversal visits every node and leaf at most once: more visits than
 // that (2 n_nodes + 1) mean a corrupt tree.  The traversal then stops and
 // records guard bit 2 (guard may be null: not recorded) instead of running on.
-__device__ __forceinline__ bool over_visit_limit(unsigned &visits, int n_nodes, unsigned int *guard) {
-    if (++visits <= 2u * (unsigned)n_nodes + 8u) return false;
+// `limit` (nonzero) sets a lower cap chosen by the caller.
+__device__ __forceinline__ bool over_visit_limit(unsigned &visits, int n_nodes, unsigned int *guard,
+                                                 unsigned limit = 0u) {
+    if (++visits <= (limit ? limit : 2u * (unsigned)n_nodes + 8u)) return false;
     if (guard) atomicOr(guard, 2u);
     return true;
 }
@@ -389,7 +392,7 @@ __device__ Closest q_closest(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &
     if (box_dist2<D>(T.root_lo, T.root_hi, x) >= best.d2) return best;
     unsigned visits = 0;
     for (;;) {
-        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
+        if (over_visit_limit(visits, T.n_nodes, st.guard, st.visit_limit)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -505,7 +508,7 @@ __device__ float q_silhouette(const TreeView &T, P3 x, float rmax, const Stack &
     uint32_t ref = T.root;
     unsigned visits = 0;
     for (;;) {
-        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
+        if (over_visit_limit(visits, T.n_nodes, st.guard, st.visit_limit)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -565,7 +568,7 @@ __device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int
     uint32_t ref = T.root;
     unsigned visits = 0;
     for (;;) {
-        if (over_visit_limit(visits, T.n_nodes, st.guard)) break;
+        if (over_visit_limit(visits, T.n_nodes, st.guard, st.visit_limit)) break;
         if (is_leaf(ref)) {
             uint32_t f = leaf_first(ref), c = leaf_count(ref);
             for (uint32_t k = f; k < f + c; ++k) {
@@ -604,6 +607,92 @@ __device__ __noinline__ int q_ray(const TreeView &T, P3 o, P3 v, float tmax, int
             if (key <= tb) break;
         }
         if (!(key <= tb)) break;
+    }
+    t_out = tb;
+    return hit;
+}
+
+// Q.3 and the visibility test of the Neumann sample in ONE traversal of the
+// Neumann tree: ray A (o + t va, 0 < t <= tmaxA, closest hit, edge margin
+// kEdgeTol) and, if wantB, ray B (o + t vb, 0 < t <= tmaxB, any hit, no
+// margin, skipping primitive skipB).  Both start at the same origin; a node
+// is visited if either ray still needs it, and each leaf primitive is loaded
+// once and tested against both.  Against two separate traversals this saves
+// the second loop, which the warp would otherwise run for the few lanes
+// whose Neumann sample is valid.  A stack entry keeps A's entry distance
+// (+inf if A misses the node) with the sign bit set when B meets the node.
+// Returns A's hit record (or -1, t_out = tmaxA) and sets occB.
+__device__ __forceinline__ float key_with_b(float ka, bool b) {
+    return __uint_as_float(__float_as_uint(ka) | (b ? 0x80000000u : 0u));
+}
+template <int D, bool CN = false>
+__device__ __noinline__ int q_ray2(const TreeView &T, P3 o, P3 va, float tmaxA, float &t_out, bool wantB, P3 vb,
+                                   int skipB, float tmaxB, bool &occB, const Stack &st, Cnt<CN> &cnt) {
+    int hit = -1;
+    float tb = tmaxA;
+    bool actB = wantB;
+    occB = false;
+    t_out = tmaxA;
+    if (T.root == WOST_EMPTY_REF) return -1;
+    const P3 ia = mk(1.f / va.x, 1.f / va.y, D == 3 ? 1.f / va.z : 0.f);
+    const P3 ib = mk(1.f / vb.x, 1.f / vb.y, D == 3 ? 1.f / vb.z : 0.f);
+    {
+        float a0 = box_ray<D>(T.root_lo, T.root_hi, o, ia, tb);
+        float b0 = actB ? box_ray<D>(T.root_lo, T.root_hi, o, ib, tmaxB) : INFINITY;
+        if (a0 == INFINITY && b0 == INFINITY) return -1;
+    }
+    int sp = 0;
+    uint32_t ref = T.root;
+    unsigned visits = 0;
+    for (;;) {
+        if (over_visit_limit(visits, T.n_nodes, st.guard, st.visit_limit)) break;
+        if (is_leaf(ref)) {
+            uint32_t f = leaf_first(ref), c = leaf_count(ref);
+            for (uint32_t k = f; k < f + c; ++k) {
+                Prim<D> p = load_prim<D>(T.prims, k);
+                float t;
+                cnt.prim(C_Q3);
+                if (prim_ray<D>(p, o, va, tb, t, kEdgeTol)) {
+                    tb = t;
+                    hit = (int)k;
+                }
+                if (actB && (int)k != skipB) {
+                    cnt.prim(C_VIS);
+                    if (prim_ray<D>(p, o, vb, tmaxB, t, 0.f)) {
+                        occB = true;
+                        actB = false;
+                    }
+                }
+            }
+        } else {
+            cnt.node(C_Q3);
+            Node<D> n = load_node<D>(T.nodes, ref);
+            float a0 = box_ray<D>(n.lo0, n.hi0, o, ia, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, ia, tb);
+            bool b0 = actB && box_ray<D>(n.lo0, n.hi0, o, ib, tmaxB) != INFINITY;
+            bool b1 = actB && box_ray<D>(n.lo1, n.hi1, o, ib, tmaxB) != INFINITY;
+            bool h0 = a0 != INFINITY || b0, h1 = a1 != INFINITY || b1;
+            if (h0 && h1) {
+                bool first0 = a0 <= a1;
+                spush(st, sp, first0 ? n.r1 : n.r0, first0 ? key_with_b(a1, b1) : key_with_b(a0, b0));
+                ref = first0 ? n.r0 : n.r1;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? n.r0 : n.r1;
+                continue;
+            }
+        }
+        // next pending subtree that either ray still needs
+        bool found = false;
+        while (sp > 0) {
+            float key;
+            spop(st, sp, ref, key);
+            if (fabsf(key) <= tb || (actB && signbit(key))) {
+                found = true;
+                break;
+            }
+        }
+        if (!found) break;
     }
     t_out = tb;
     return hit;
@@ -831,12 +920,12 @@ struct LaneQ {
         return q_ray<D, CN>(T, o, v, tmax, skip, any, t, st, cnt);
     }
     __device__ NSample sample(const TreeView &T, P3 x, float r, Stream &rng) { return q_sample<D, CN>(T, x, r, rng, cnt); }
+    __device__ int ray2(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
+                        float tmaxB, bool &occB) {
+        return q_ray2<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt);
+    }
 };
 
-// One iteration of Alg. 1.  Returns true when the walk has terminated (its
-// estimate is then w.acc).  Q answers the geometric queries (LaneQ: one lane
-// per walk; GroupQ: 8 cooperating lanes per walk, every lane of the group
-// running this same code on the same walk).
 // R13: inside the grown bounding box (false for a non-finite position)
 template <int D>
 __device__ __forceinline__ bool in_bounds(const SceneView &sc, P3 x) {
@@ -845,40 +934,78 @@ __device__ __forceinline__ bool in_bounds(const SceneView &sc, P3 x) {
     return in;
 }
 
+// One iteration of Alg. 1 for the walk w of this lane (act = the lane holds
+// a walk).  Returns true when an active walk has terminated (its estimate is
+// then w.acc).  Q answers the geometric queries (LaneQ: one lane per walk;
+// GroupQ: 8 cooperating lanes per walk, every lane of the group running this
+// same code on the same walk).
+//
+// Warp-synchronous: all 32 lanes of the warp call it together, and the warp
+// meets at a __syncwarp() after every query.  Without those meeting points
+// the lanes that finish a traversal early run ahead into the next query
+// while the others are still traversing, and the warp splits into small
+// groups that each issue the whole step on their own (measured: 5 of 32
+// lanes per query call on the Koch workload, 2 in 3D).  Inactive lanes only
+// take part in the meetings; every __syncwarp() here is reached by every
+// lane (conditions on it are warp-uniform).
+//
 // SCR: compiled with the screened-equation terms (R15); the Poisson-only
 // instantiation keeps them, and their registers, out of the hot loop.
 template <int D, bool SCR, class Q>
-__device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q &q) {
+__device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q &q, bool act) {
+    constexpr unsigned FULL = 0xffffffffu;
     // R13: a walk outside the grown bounding box of the boundary has left the
     // domain through a rounding gap; it ends like a capped walk (R5)
-    const bool lost = !in_bounds<D>(sc, w.x);
+    const bool lost = act && !in_bounds<D>(sc, w.x);
     // distance to the Dirichlet boundary (Q.1).  The closest point of the
     // previous step is at most dbound away (triangle inequality), which
-    // prunes the search; the result is the exact closest point either way.
-    float b = w.dbound * 1.0001f + 1e-6f;
+    // prunes the search; the result is the exact closest point either way,
+    // and a walk whose bound excluded everything searches again without it.
+    const float b = w.dbound * 1.0001f + 1e-6f;
     Closest cl;
+    cl.d2 = INFINITY;
+    cl.rec = -1;
+    cl.s0 = cl.s1 = 0.f;
+    cl.p = w.x;
+    bool need = act;
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {  // one call site keeps the code small
-        cl = q.closest(sc.D, w.x, pass == 0 ? b * b : INFINITY);
-        if (cl.rec >= 0) break;
-    }
-    w.steps += 1;
-    float dD = sqrtf(cl.d2);
-    if (dD < sp.epsilon || w.steps >= sp.max_steps || lost) {
-        // epsilon shell: g at the closest point (R5: also at the step cap)
-        w.capped = !(dD < sp.epsilon);
-        if (cl.rec >= 0) {
-            float gv = sc.g.kind == FIELD_ANALYTIC ? fn_u<D>(sc.g.fn, sc.g.params, cl.p)
-                                                   : corner_interp<D>(sc.D.data, cl.rec, cl.s0, cl.s1);
-            w.acc += gv;
+        if (!__any_sync(FULL, need)) break;
+        if (need) {
+            cl = q.closest(sc.D, w.x, pass == 0 ? b * b : INFINITY);
+            need = cl.rec < 0;
         }
-        return true;
+        __syncwarp();
     }
+    bool ended = false;
+    const float dD = sqrtf(cl.d2);
+    if (act) {
+        w.steps += 1;
+        if (dD < sp.epsilon || w.steps >= sp.max_steps || lost) {
+            // epsilon shell: g at the closest point (R5: also at the step cap)
+            w.capped = !(dD < sp.epsilon);
+            if (cl.rec >= 0) {
+                // App. B: on a double-sided primitive, the - side's data if x
+                // lies on the side its normal points into
+                const float4 *gd = sc.D.data;
+                if (sc.D.sided && sc.D.sided[cl.rec] &&
+                    !(dotp<D>(cl.p - w.x, prim_normal<D>(load_prim<D>(sc.D.prims, (uint32_t)cl.rec))) > 0.f))
+                    gd = sc.D.data_minus;
+                float gv = sc.g.kind == FIELD_ANALYTIC ? fn_u<D>(sc.g.fn, sc.g.params, cl.p)
+                                                       : corner_interp<D>(gd, cl.rec, cl.s0, cl.s1);
+                w.acc += gv;
+            }
+            ended = true;
+        }
+    }
+    act = act && !ended;
     // R4: query origin off the Neumann boundary
-    float delta = sp.offset * (1.f + maxabs3(w.x));
-    P3 xq = w.onN ? w.x - w.n * delta : w.x;
+    const float delta = sp.offset * (1.f + maxabs3(w.x));
+    const P3 xq = w.onN ? w.x - w.n * delta : w.x;
     // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
-    float dsil = q.silhouette(sc.S, xq, dD);
+    float dsil = dD;
+    if (act) dsil = q.silhouette(sc.S, xq, dD);
+    __syncwarp();
     float r = fminf(dD, fmaxf(sp.r_min, dsil));
     // R14: at most the scene's diameter, which matters only without Dirichlet
     // data; such scenes are solved with sigma > 0, i.e. in the screened
@@ -888,8 +1015,9 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     float sqs = 0.f;
     if constexpr (SCR) sqs = (sp.sigma > 0.f && w.steps - 1 >= sp.screen_after) ? sp.sqrt_sigma : 0.f;
     // direction: uniform, flipped into the hemisphere about -n_x on the boundary
-    uint32_t k = (uint32_t)(w.steps - 1);
-    uint4 rb = philox10(make_uint4(w.index, w.point, k, 0u), sp.key0, sp.key1);
+    const uint32_t k = (uint32_t)(w.steps - 1);
+    uint4 rb = make_uint4(0u, 0u, 0u, 0u);
+    if (act) rb = philox10(make_uint4(w.index, w.point, k, 0u), sp.key0, sp.key1);
     P3 v;
     if constexpr (D == 2) {
         float s, c;
@@ -903,49 +1031,65 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
         v = mk(rr * c, rr * s, zc);
     }
     if (w.onN && dotp<D>(w.n, v) > 0.f) v = v * -1.f;
-    // first hit with the Neumann part of the star boundary (Q.3)
-    float th;
-    int hrec = q.ray(sc.N, xq, v, r, -1, false, th);
+    // Neumann contribution from a separate sample z (Q.4) if h is present
+    const bool hzero = sc.h.kind == FIELD_ANALYTIC && sc.h.fn == 0;
+    const bool want4 = act && !hzero && sc.N.root != WOST_EMPTY_REF;
+    NSample zs;
+    zs.rec = -1;
+    zs.pdf = 0.f;
+    zs.z = w.x;
+    zs.s0 = zs.s1 = 0.f;
+    if (__any_sync(FULL, want4)) {
+        if (want4) {
+            Stream rng;
+            rng.init(sp.key0, sp.key1, w.index, w.point, k);
+            zs = q.sample(sc.N, w.x, r, rng);
+        }
+        __syncwarp();
+    }
+    // R12: a sample at zero distance (x and z rounded onto the same point of
+    // one primitive) has G = inf and measure zero: skipped
+    const P3 dz = zs.z - w.x;
+    const float dzl = sqrtf(dotp<D>(dz, dz));
+    const bool wantv = want4 && zs.rec >= 0 && zs.pdf > 0.f && dzl < r && dzl > 0.f;
+    // first hit with the Neumann part of the star boundary (Q.3) and the
+    // visibility of z (one traversal for both rays)
+    float th = r;
+    int hrec = -1;
+    bool occ = false;
+    if (act) hrec = q.ray2(sc.N, xq, v, r, th, wantv, zs.z - xq, zs.rec, sp.vis_tmax, occ);
+    __syncwarp();
+    if (!act) return ended;
     P3 p, np = mk(0.f, 0.f, 0.f);
     if (hrec >= 0) {
         p = xq + v * th;
         np = prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)hrec));
+        // App. B: a double-sided sheet is hit from the side the walk is on;
+        // its outward normal there is the one the walk moves along
+        if (sc.N.sided && sc.N.sided[hrec] && dotp<D>(v, np) < 0.f) np = np * -1.f;
     } else {
         p = w.x + v * r;
     }
-    // Neumann contribution from a separate sample z (Q.4) if h is present
     float Nterm = 0.f;
-    bool hzero = sc.h.kind == FIELD_ANALYTIC && sc.h.fn == 0;
-    if (!hzero && sc.N.root != WOST_EMPTY_REF) {
-        Stream rng;
-        rng.init(sp.key0, sp.key1, w.index, w.point, k);
-        NSample zs = q.sample(sc.N, w.x, r, rng);
-        if (zs.rec >= 0 && zs.pdf > 0.f) {
-            P3 dz = zs.z - w.x;
-            float dzl = sqrtf(dotp<D>(dz, dz));
-            // R12: a sample at zero distance (x and z rounded onto the same
-            // point of one primitive) has G = inf and measure zero: skipped
-            if (dzl < r && dzl > 0.f) {
-                float tv;
-                int occ = q.ray(sc.N, xq, zs.z - xq, sp.vis_tmax, zs.rec, true, tv);
-                if (occ < 0) {
-                    float hv;
-                    if (sc.h.kind == FIELD_ANALYTIC) {
-                        P3 nz = prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)zs.rec));
-                        hv = dotp<D>(fn_grad<D>(sc.h.fn, sc.h.params, zs.z), nz);
-                    } else {
-                        hv = corner_interp<D>(sc.N.data, zs.rec, zs.s0, zs.s1);
-                    }
-                    float G = D == 2 ? logf(r / dzl) * (0.5f / 3.14159265358979f)
-                                     : (1.f / dzl - 1.f / r) * (0.25f / 3.14159265358979f);
-                    if constexpr (SCR) {
-                        if (sqs > 0.f) G = screened_green<D>(dzl, r, sqs);
-                    }
-                    float alpha = w.onN ? 0.5f : 1.f;
-                    Nterm = G * hv / (alpha * zs.pdf);
-                }
-            }
+    if (wantv && !occ) {
+        float hv;
+        // App. B: the data of the side of a double-sided sheet that faces the
+        // query point (offset onto the walk's side when it lies on a sheet)
+        const bool minus = sc.N.sided && sc.N.sided[zs.rec] &&
+                           !(dotp<D>(zs.z - xq, prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)zs.rec))) > 0.f);
+        if (sc.h.kind == FIELD_ANALYTIC) {
+            P3 nz = prim_normal<D>(load_prim<D>(sc.N.prims, (uint32_t)zs.rec));
+            hv = dotp<D>(fn_grad<D>(sc.h.fn, sc.h.params, zs.z), minus ? nz * -1.f : nz);
+        } else {
+            hv = corner_interp<D>(minus ? sc.N.data_minus : sc.N.data, zs.rec, zs.s0, zs.s1);
         }
+        float G = D == 2 ? logf(r / dzl) * (0.5f / 3.14159265358979f)
+                         : (1.f / dzl - 1.f / r) * (0.25f / 3.14159265358979f);
+        if constexpr (SCR) {
+            if (sqs > 0.f) G = screened_green<D>(dzl, r, sqs);
+        }
+        float alpha = w.onN ? 0.5f : 1.f;
+        Nterm = G * hv / (alpha * zs.pdf);
     }
     // source contribution, reusing the direction v (Sec. 4.6)
     float Sterm = 0.f;

@@ -41,7 +41,7 @@ struct Request {
     int64_t cursor = 0;                  // next point of the stage to issue
     int outstanding = 0;                 // pieces in flight
     double mean_steps = 64.0;            // running estimate of steps per walk
-    bool admitted = false, finished = false;
+    bool admitted = false, finished = false, started = false;
 };
 
 struct Piece {
@@ -88,6 +88,8 @@ struct wost_engine {
     cudaStream_t stream = nullptr, check_stream = nullptr;
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
+    double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
+    double min_round_steps = 1e5;     // keeps the resident grid supplied with walks
     int min_walks = 16, cap = 65536, block = 128;
     std::mutex mu;
     std::condition_variable cv, done_cv;
@@ -97,7 +99,6 @@ struct wost_engine {
     std::deque<Round> inflight;
     Slot slots[3];
     double round_budget_steps = 4e6;
-    size_t rr = 0;
     wost_engine_stats st{};
     bool stop = false;
     std::thread th;
@@ -318,30 +319,42 @@ bool launch_round(wost_engine *e) {
             break;
         }
     if (si < 0) return false;
+    // overload shedding: requests that waited too long for their first
+    // walks, admitted or still queued for memory
+    if (e->max_wait > 0) {
+        std::vector<Request *> late;
+        for (Request *r : e->active)
+            if (!r->finished && !r->started && r->outstanding == 0 && since(r->t_submit) > e->max_wait)
+                late.push_back(r);
+        for (Request *r : e->pending)
+            if (!r->finished && since(r->t_submit) > e->max_wait) late.push_back(r);
+        for (Request *r : late) {
+            e->st.rejected++;
+            e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), r), e->pending.end());
+            finish(e, r, WOST_ERR_TIMEOUT);
+        }
+    }
+    // active requests in admission order (the order of e->active)
     std::vector<Request *> iss;
     for (Request *r : e->active)
         if (!r->finished && r->cursor < r->h->n_points && !cancelled(r)) iss.push_back(r);
     if (iss.empty()) return false;
     Round rd;
     rd.slot = si;
-    size_t n = iss.size();
-    size_t start = e->rr++ % n;
-    double remaining = e->round_budget_steps, share = remaining / (double)n;
-    for (int pass = 0; pass < 2 && remaining > 0; ++pass) {
-        for (size_t k = 0; k < n && remaining > 0; ++k) {
-            Request *r = iss[(start + k) % n];
-            int64_t left = r->h->n_points - r->cursor;
-            if (left <= 0) continue;
-            double cost = (double)(r->stage_end - r->stage_begin) * r->mean_steps;
-            double allow = pass == 0 ? share : remaining;
-            int64_t np = (int64_t)(allow / cost);
-            if (pass == 1 && np < 1) continue;
-            np = std::max<int64_t>(1, std::min(np, left));
-            rd.pieces.push_back(Piece{r, r->cursor, np, r->stage_begin, r->stage_end - r->stage_begin});
-            r->cursor += np;
-            r->outstanding++;
-            remaining -= (double)np * cost;
-        }
+    // the round's budget goes to the oldest requests first: each takes as
+    // many points of its current stage as the remaining budget pays for
+    // (at least one point, so every round makes progress)
+    double remaining = std::max(e->round_budget_steps, e->min_round_steps);
+    for (Request *r : iss) {
+        if (remaining <= 0) break;
+        int64_t left = r->h->n_points - r->cursor;
+        double cost = (double)(r->stage_end - r->stage_begin) * r->mean_steps;
+        int64_t np = std::max<int64_t>(1, std::min<int64_t>((int64_t)(remaining / cost), left));
+        rd.pieces.push_back(Piece{r, r->cursor, np, r->stage_begin, r->stage_end - r->stage_begin});
+        r->cursor += np;
+        r->outstanding++;
+        r->started = true;
+        remaining -= (double)np * cost;
     }
     // job tables per dimension, written into the slot's pinned staging
     Slot &sl = e->slots[si];
@@ -463,12 +476,21 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
         std::unique_ptr<wost_engine> e(new wost_engine);
         e->device = d->device;
         e->round_seconds = d->round_seconds > 0 ? d->round_seconds : 0.02;
+        if (!(d->max_wait_seconds >= 0)) return fail(WOST_ERR_INVALID_ARG, "max_wait_seconds must be >= 0");
+        e->max_wait = d->max_wait_seconds;
         e->min_walks = d->min_walks ? d->min_walks : 16;
         e->cap = d->max_walks_per_point ? d->max_walks_per_point : 65536;
         e->block = block;
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
         e->budget = d->memory_budget_bytes ? d->memory_budget_bytes : (int64_t)(fr / 4);
+        {
+            // a round must give every resident lane several walks, else its
+            // time is that of its longest walk with the grid mostly idle
+            int blocks3 = 0;
+            CK(batch_grid(3, block, 64, &blocks3), "occupancy");
+            e->min_round_steps = 4.0 * 64.0 * (double)blocks3 * block;
+        }
         CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         CK(cudaStreamCreateWithFlags(&e->check_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         for (auto &s : e->slots) {

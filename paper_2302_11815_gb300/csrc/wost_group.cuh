@@ -355,6 +355,18 @@ struct GroupQ {
         out.rec = (int)(f + (uint32_t)k);
         return out;
     }
+
+    // Q.3 and the visibility test: two traversals of the wide tree
+    __device__ int ray2(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
+                        float tmaxB, bool &occB) {
+        int h = ray(T, o, va, tmaxA, -1, false, t);
+        occB = false;
+        if (wantB) {
+            float tv;
+            occB = ray(T, o, vb, tmaxB, skipB, true, tv) >= 0;
+        }
+        return h;
+    }
 };
 
 }  // namespace wost

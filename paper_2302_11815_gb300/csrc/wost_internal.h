@@ -64,6 +64,8 @@ struct TreeView {
     const float4 *cones;    // 2 float4 per node (S only)
     const float4 *prims;    // records, see above
     const float4 *data;     // D/N corner data (2D: reinterpret as float2)
+    const float4 *data_minus;  // D/N corner data of the - side of double-sided records (or null)
+    const uint8_t *sided;   // per record: 1 = double-sided (App. B); null if none is
     const int32_t *ids;     // input index of each record
     uint32_t root;          // child reference of the root (or WOST_EMPTY_REF)
     float root_lo[3], root_hi[3];
@@ -101,6 +103,7 @@ struct SolveParams {
     float offset;               // relative ray-origin offset on the boundary
     float vis_tmax;             // visibility ray end for the Neumann sample
     int32_t stack_depth;        // shared-memory stack entries per walk (thread or team)
+    uint32_t visit_limit;       // node visits allowed per traversal (0: 2 n_nodes + 8)
     float sigma;                // screening coefficient (0: Poisson)
     float sqrt_sigma;
     int32_t screen_after;       // steps k >= screen_after are screened (Tikhonov switch)

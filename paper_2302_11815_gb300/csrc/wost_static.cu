@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "capi_internal.h"
 
@@ -49,22 +48,17 @@ __global__ void k_static_finish(const unsigned char *scratch, int64_t n, float *
     if (se) se[i] = guard ? nan : (float)(c > 0 ? sqrt(v / c) : 0.0);
 }
 
-// Device address of the scratch array on `device` (which must be current),
-// looked up on the first call per device.  The lookup can load the module,
-// which a stream capture does not allow: the first call on a device must
-// come before any capture.
-static cudaError_t scratch_address(int device, unsigned char **out) {
-    static std::mutex mu;
-    static unsigned char *addr[64] = {};
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[device]) {
-        unsigned char *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        addr[device] = p;
-    }
-    *out = addr[device];
+// Device address of the scratch array on the current device, looked up on
+// every call: a cached address would outlive a device reset or a recreated
+// primary context, after which it points at freed memory.  The lookup is a
+// host-side table read once the module is loaded; the first one on a device
+// can load the module, which a stream capture does not allow, so the first
+// call on a device must come before any capture.
+static cudaError_t scratch_address(unsigned char **out) {
+    unsigned char *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -91,7 +85,7 @@ extern "C" wost_status wost_solve_static(wost_scene *scene, int64_t n_points, co
     cudaStream_t stream = (cudaStream_t)stream_arg;
     CK(cudaSetDevice(scene->device), "cudaSetDevice");
     unsigned char *s = nullptr;
-    CK(scratch_address(scene->device, &s), "cudaGetSymbolAddress");
+    CK(scratch_address(&s), "cudaGetSymbolAddress");
     const size_t n = (size_t)n_points;
     // the array keeps the previous call's contents: clear the counters and
     // the first n entries of each accumulator array

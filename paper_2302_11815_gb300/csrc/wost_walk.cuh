@@ -70,10 +70,11 @@ using WalkQ = GroupQ<D, CN>;
 
 // the query policy of this thread's team, with its shared-memory stack
 template <int D, bool CN>
-__device__ __forceinline__ WalkQ<D, CN> make_q(int depth, unsigned int *guard, Cnt<CN> &cnt) {
+__device__ __forceinline__ WalkQ<D, CN> make_q(int depth, unsigned int *guard, Cnt<CN> &cnt,
+                                               uint32_t visit_limit = 0u) {
     extern __shared__ int2 smem_stack[];
 #if WOST_TEAM == 1
-    Stack s{smem_stack + threadIdx.x, (int)blockDim.x, depth, guard};
+    Stack s{smem_stack + threadIdx.x, (int)blockDim.x, depth, guard, visit_limit};
     return LaneQ<D, CN>{s, cnt};
 #else
     GStack s{smem_stack + (threadIdx.x / WOST_TEAM) * depth, depth, guard};
@@ -101,21 +102,21 @@ template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     int warp_uniform_points) {
     Cnt<false> cnt;
-    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
     const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
     const bool active = gid < total && !team_flag(g, acc.cancel);
-    Walk w;
+    Walk w{};
     if (active) {
         int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
         uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
         walk_init<D>(sp, w, pt, j);
     }
-    // the warp reconverges after every step (see k_walk_persistent)
+    // the whole warp steps together (walk_step is warp-synchronous)
     bool done = !active;
     while (__any_sync(0xffffffffu, !done)) {
-        if (!done) done = walk_step<D, SCR>(sc, sp, w, q);
+        if (walk_step<D, SCR>(sc, sp, w, q, !done)) done = true;
         __syncwarp();
     }
     const bool own = active && g.leader();  // one lane reports each walk
@@ -150,17 +151,19 @@ template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
     Cnt<false> cnt;
-    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
     const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    Walk w;
+    Walk w{};
     bool have = false, drained = false;  // uniform within a team
-    // All 32 lanes stay in this loop until the warp runs out of work and meet
-    // at __syncwarp() after every walk step, so the warp starts each step
-    // converged (without it, independent thread scheduling lets the lanes
-    // drift apart and issue alone).
+    // All 32 lanes stay in this loop until the warp runs out of work, call
+    // the warp-synchronous walk_step together (lanes without a walk take part
+    // in its meetings only) and meet at __syncwarp() after every walk step,
+    // so the warp starts each step and each query converged (without it,
+    // independent thread scheduling lets the lanes drift apart and issue
+    // alone).
     for (;;) {
         // regeneration: teams without a walk take the next ones (one ballot
         // bit per team, on its leader)
@@ -186,11 +189,9 @@ __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const Sol
             }
         }
         if (!__any_sync(FULL, have)) break;
-        if (have) {
-            if (walk_step<D, SCR>(sc, sp, w, q)) {
-                if (g.leader()) accumulate(acc, w);
-                have = false;
-            }
+        if (walk_step<D, SCR>(sc, sp, w, q, have)) {
+            if (g.leader()) accumulate(acc, w);
+            have = false;
         }
         __syncwarp();
     }
@@ -206,13 +207,13 @@ template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolveParams sp,
                                                      const Accumulators acc, const ResumeState rs, int iters) {
     Cnt<false> cnt;
-    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt);
+    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
     const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     float4 *slot = rs.slots + 3 * (((size_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM);
-    Walk w;
+    Walk w{};
     bool have = false, drained = false;  // uniform within a team
     {
         float4 c = slot[2];
@@ -255,12 +256,10 @@ __global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolvePa
             }
         }
         if (!__any_sync(FULL, have)) break;
-        if (have) {
-            ++ran;
-            if (walk_step<D, SCR>(sc, sp, w, q)) {
-                if (g.leader()) accumulate(acc, w);
-                have = false;
-            }
+        if (have) ++ran;
+        if (walk_step<D, SCR>(sc, sp, w, q, have)) {
+            if (g.leader()) accumulate(acc, w);
+            have = false;
         }
         __syncwarp();
     }
@@ -302,7 +301,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hd
     const Group g = make_team();
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    Walk w;
+    Walk w{};
     int job = -1;
     bool drained = false;  // the launch's counter has run past `total`
     // as in k_walk_persistent: the whole warp stays in the loop and
@@ -342,11 +341,11 @@ __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hd
             }
         }
         if (!__any_sync(FULL, job >= 0 || !drained)) break;
-        if (job >= 0) {
-            if (walk_step<D, true>(*jobs[job].scene, jobs[job].sp, w, q)) {
-                if (g.leader()) accumulate(jobs[job].acc, w);
-                job = -1;
-            }
+        // lanes without a job step a dummy reference to job 0 (inactive)
+        const BatchJob &J = jobs[job >= 0 ? job : 0];
+        if (walk_step<D, true>(*J.scene, J.sp, w, q, job >= 0)) {
+            if (g.leader()) accumulate(J.acc, w);
+            job = -1;
         }
         __syncwarp();
     }
@@ -358,18 +357,23 @@ template <int D, bool SCR>
 __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const SolveParams sp, const Accumulators acc,
                                                     unsigned long long *stats) {
     Cnt<true> cnt;
-    auto q = make_q<D, true>(sp.stack_depth, acc.guard, cnt);
+    auto q = make_q<D, true>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
     const Group g = make_team();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
-    if (gid >= total) return;
-    Walk w;
-    int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
-    uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
-    walk_init<D>(sp, w, pt, j);
-    while (!walk_step<D, SCR>(sc, sp, w, q)) {
+    const bool active = gid < total;
+    Walk w{};
+    if (active) {
+        int64_t pt = (int64_t)(gid / (uint64_t)sp.walks_per_point);
+        uint32_t j = (uint32_t)(gid % (uint64_t)sp.walks_per_point) + sp.first_walk;
+        walk_init<D>(sp, w, pt, j);
     }
-    if (!g.leader()) return;
+    bool done = !active;
+    while (__any_sync(0xffffffffu, !done)) {
+        if (walk_step<D, SCR>(sc, sp, w, q, !done)) done = true;
+        __syncwarp();
+    }
+    if (!active || !g.leader()) return;
     accumulate(acc, w);
     for (int c = 0; c < C_NQ; ++c) {
         atomicAdd(stats + c, (unsigned long long)cnt.nodes[c]);

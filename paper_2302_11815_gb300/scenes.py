@@ -70,6 +70,10 @@ def exact_u(fn: str, params, pts: np.ndarray) -> np.ndarray:
         return p[0] + p[1] * np.log(rho) if dim == 2 else p[0] + p[1] / rho
     if fn == "exp_plane":
         return p[0] * np.exp(p[1] * X + p[2] * Y + p[3] * Z)
+    if fn == "polar_angle":
+        return np.mod(np.arctan2(Y, X), 2 * np.pi)
+    if fn == "crack_mode":
+        return np.sqrt(np.hypot(X, Y)) * np.cos(np.mod(np.arctan2(Y, X), 2 * np.pi) / 2)
     raise ValueError(fn)
 
 
@@ -606,6 +610,132 @@ def ball_points(rng, n, dim, radius):
     x /= np.linalg.norm(x, axis=1, keepdims=True)
     r = radius * rng.random(n) ** (1.0 / dim)
     return (x * r[:, None]).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Double-sided boundaries (App. B): a slit and thin Neumann sheets
+# ---------------------------------------------------------------------------
+def _square_loop(m):
+    """Vertices of the square [-1,1]^2, CCW, m segments per side, starting at
+    (1, 0) (so that (1, 0) is a vertex)."""
+    t = np.arange(4 * m) / (4 * m)
+    pts = []
+    for k in range(4 * m):
+        # perimeter parameter from (1, 0) going up the right side
+        s = 8.0 * t[k]
+        if s < 1:
+            pts.append((1.0, s))
+        elif s < 3:
+            pts.append((1.0 - (s - 1), 1.0))
+        elif s < 5:
+            pts.append((-1.0, 1.0 - (s - 3)))
+        elif s < 7:
+            pts.append((-1.0 + (s - 5), -1.0))
+        else:
+            pts.append((1.0, -1.0 + (s - 7)))
+    return np.array(pts)
+
+
+def polar_angle(pts):
+    """Angle in [0, 2 pi) measured from the positive x axis: harmonic off
+    the cut along the positive x axis."""
+    return np.mod(np.arctan2(pts[:, 1], pts[:, 0]), 2 * np.pi)
+
+
+def slit_square_scene(m=16, n_slit=16):
+    """The square [-1,1]^2 with a slit from (0, 0) to (1, 0): a double-sided
+    Dirichlet segment chain (flag 2).  u = the polar angle in [0, 2 pi),
+    harmonic in the slit square; it is 0 on the slit's upper side and 2 pi
+    on its lower side.  The slit runs along +x, so its normal n+ = (0, -1):
+    its + side (the one n+ points away from) is the upper one, g+ = 0,
+    g- = 2 pi.  Box data per corner, each segment on its own branch of the
+    angle (the right side's segments above and below (1, 0) differ)."""
+    Vb = _square_loop(m)
+    nb = len(Vb)
+    xs = np.linspace(0.0, 1.0, n_slit + 1)
+    Vs = np.c_[xs, np.zeros_like(xs)]
+    V = np.concatenate([Vb, Vs])
+    Pb = closed_polyline(Vb)
+    Ps = np.c_[np.arange(n_slit), np.arange(1, n_slit + 1)] + nb
+    P = np.concatenate([Pb, Ps])
+    flags = np.concatenate([np.zeros(len(Pb)), np.full(n_slit, 2)]).astype(np.uint8)
+    mid = 0.5 * (V[P[:, 0]] + V[P[:, 1]])
+    th_mid = polar_angle(mid)
+    g = np.zeros((len(P), 2))
+    for k in range(2):
+        c = V[P[:, k]]
+        d = np.arctan2(c[:, 1], c[:, 0]) - th_mid
+        g[:, k] = th_mid + (d + np.pi) % (2 * np.pi) - np.pi  # the corner on its segment's branch
+    ns = len(Pb)
+    g[ns:] = 0.0
+    gm = np.zeros_like(g)
+    gm[ns:] = 2 * np.pi
+    return {"dim": 2, "vertices": V.astype(np.float32), "prims": P.astype(np.int32), "flags": flags,
+            "g": {"kind": "per_corner", "values": g.astype(np.float32)},
+            "g_minus": {"kind": "per_corner", "values": gm.astype(np.float32)},
+            "h": {"kind": "none"}, "f": {"kind": "none"}, "exact": ("polar_angle", [])}
+
+
+def crack_square_scene(m=16, n_slit=16):
+    """The square [-1,1]^2 with a crack from (0, 0) to (1, 0): a
+    double-sided Neumann segment chain (flag 3) with zero flux on both
+    sides.  u = sqrt(rho) cos(theta / 2), theta in [0, 2 pi), is harmonic off
+    the crack with zero normal derivative on both of its sides, and jumps
+    from sqrt(rho) above to -sqrt(rho) below: a walk that crossed the crack
+    would pick up the other side's values.  Dirichlet data on the box per
+    corner, each segment on its own branch of theta."""
+    sc = slit_square_scene(m, n_slit)
+    V, P = sc["vertices"].astype(np.float64), sc["prims"]
+    ns = len(P) - n_slit
+    theta = sc["g"]["values"].astype(np.float64)  # per-corner angle on each box segment's branch
+    rho = np.stack([np.hypot(V[P[:, k], 0], V[P[:, k], 1]) for k in range(2)], 1)
+    g = np.sqrt(rho) * np.cos(theta / 2)
+    g[ns:] = 0.0
+    flags = sc["flags"].copy()
+    flags[ns:] = 3
+    return {"dim": 2, "vertices": sc["vertices"], "prims": P, "flags": flags,
+            "g": {"kind": "per_corner", "values": g.astype(np.float32)},
+            "h": {"kind": "per_corner", "values": np.zeros((len(P), 2), np.float32)},
+            "f": {"kind": "none"}, "exact": ("crack_mode", [])}
+
+
+def sheet_square_scene(m=8, n_sheet=16, y0=0.1, half=0.5, params=(0.5, 0.3, 1.5, 0.0), data="analytic"):
+    """The Dirichlet square [-1,1]^2 with a double-sided Neumann sheet (flag
+    3) from (-half, y0) to (half, y0) inside, u linear (harmonic).  The sheet
+    runs along +x: n+ = (0, -1), h+ = du/dn+ = -p2, h- = +p2.  data:
+    "analytic", or "per_corner" with h- given ("per_corner_minus") or left
+    NONE (then h- = -h+)."""
+    Vb = _square_loop(m)
+    xs = np.linspace(-half, half, n_sheet + 1)
+    Vs = np.c_[xs, np.full_like(xs, y0)]
+    V = np.concatenate([Vb, Vs])
+    Pb = closed_polyline(Vb)
+    Ps = np.c_[np.arange(n_sheet), np.arange(1, n_sheet + 1)] + len(Vb)
+    P = np.concatenate([Pb, Ps])
+    flags = np.concatenate([np.zeros(len(Pb)), np.full(n_sheet, 3)]).astype(np.uint8)
+    sc = _make(2, V, P, flags, "linear", params, False, "analytic" if data == "analytic" else "per_corner")
+    if data == "per_corner_minus":
+        h = sc["h"]["values"].copy()
+        sc["h_minus"] = {"kind": "per_corner", "values": (-h).astype(np.float32)}
+        sc["h_minus"]["values"][: len(Pb)] = 0.0
+    return sc
+
+
+def plate_cube_scene(m=3, k=4, z0=0.1, half=0.5, params=(0.5, 0.3, -0.4, 1.5)):
+    """The Dirichlet cube [-1,1]^3 with a double-sided Neumann square plate
+    (flag 3) at z = z0 over [-half, half]^2, k x k quads, u linear
+    (analytic data)."""
+    Vc, Pc = cube_mesh(m)
+    g = np.linspace(-half, half, k + 1)
+    A, B = np.meshgrid(g, g, indexing="ij")
+    Vp = np.c_[A.ravel(), B.ravel(), np.full(A.size, z0)]
+    idx = np.arange((k + 1) ** 2).reshape(k + 1, k + 1)
+    a = idx[:-1, :-1].ravel(); b = idx[1:, :-1].ravel(); c = idx[1:, 1:].ravel(); d = idx[:-1, 1:].ravel()
+    Pp = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)]) + len(Vc)
+    V = np.concatenate([Vc, Vp])
+    P = np.concatenate([Pc, Pp])
+    flags = np.concatenate([np.zeros(len(Pc)), np.full(len(Pp), 3)]).astype(np.uint8)
+    return _make(3, V, P, flags, "linear", params, False, "analytic")
 
 
 # ---------------------------------------------------------------------------

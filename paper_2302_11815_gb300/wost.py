@@ -26,7 +26,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "BUDGET", "CUDA", "TIMEOUT
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
 FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6,
       "exp_plane": 7}
-ABI_VERSION = 2  # WOST_ABI_VERSION of the header these structures mirror
+ABI_VERSION = 3  # WOST_ABI_VERSION of the header these structures mirror
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL = {"plain": 0, "persistent": 1, "counting": 2, "resumable": 3}
 COUNT_NAMES = ("q1", "q2", "q3", "q4", "vis")
@@ -48,7 +48,7 @@ class wost_scene_desc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("vertices", C.POINTER(C.c_float)),
                 ("n_prims", C.c_int64), ("prims", C.POINTER(C.c_int32)), ("flags", C.POINTER(C.c_uint8)),
                 ("g", wost_field), ("h", wost_field), ("f", wost_field), ("device", C.c_int32),
-                ("leaf_size", C.c_int32)]
+                ("leaf_size", C.c_int32), ("g_minus", wost_field), ("h_minus", wost_field)]
 
 
 class wost_scene_info(C.Structure):
@@ -60,7 +60,8 @@ class wost_scene_info(C.Structure):
                 ("lanes_per_walk", C.c_int32), ("node_bytes", C.c_int32), ("cone_bytes", C.c_int32),
                 ("wide_nodes_dirichlet", C.c_int64), ("wide_nodes_neumann", C.c_int64),
                 ("wide_nodes_silhouette", C.c_int64), ("wide_depth_dirichlet", C.c_int32),
-                ("wide_depth_neumann", C.c_int32), ("wide_depth_silhouette", C.c_int32)]
+                ("wide_depth_neumann", C.c_int32), ("wide_depth_silhouette", C.c_int32), ("device", C.c_int32),
+                ("stack_depth", C.c_int32)]
 
 
 class wost_solve_desc(C.Structure):
@@ -68,7 +69,8 @@ class wost_solve_desc(C.Structure):
                 ("on_neumann", C.c_void_p), ("memory", C.c_int32), ("walks_per_point", C.c_int32),
                 ("epsilon", C.c_float), ("r_min", C.c_float), ("max_steps", C.c_int32), ("seed", C.c_uint64),
                 ("first_walk", C.c_uint32), ("kernel", C.c_int32), ("block_size", C.c_int32),
-                ("stream", C.c_void_p), ("sigma", C.c_float), ("screen_after", C.c_int32)]
+                ("stream", C.c_void_p), ("sigma", C.c_float), ("screen_after", C.c_int32),
+                ("stack_depth", C.c_int32), ("visit_limit", C.c_int32)]
 
 
 class wost_progress(C.Structure):
@@ -101,6 +103,7 @@ _SIGS = {
                               C.c_void_p],
     "wost_solve_static": [C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_int32, C.c_uint64,
                           C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p],
+    "wost_read_probe": [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p],
     "wost_query_closest_dirichlet": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p],
     "wost_query_silhouette": [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -120,16 +123,19 @@ def load(path: str | None = None):
             if not os.path.exists(p):
                 raise OSError(f"libwost.so not built ({p}); run __graft_entry__.build()")
             lib = C.CDLL(p)
+            # the version first: a library of another version may lack
+            # symbols this binding declares
+            lib.wost_abi_version.restype = C.c_int32
+            lib.wost_abi_version.argtypes = []
+            if lib.wost_abi_version() != ABI_VERSION:
+                raise OSError(f"{p}: ABI version {lib.wost_abi_version()}, this binding needs {ABI_VERSION}; "
+                              "rebuild the library")
             for name, argt in _SIGS.items():
                 fn = getattr(lib, name)
                 fn.argtypes = argt
                 fn.restype = C.c_int
             lib.wost_last_error.restype = C.c_char_p
             lib.wost_last_error.argtypes = []
-            lib.wost_abi_version.restype = C.c_int32
-            if lib.wost_abi_version() != ABI_VERSION:
-                raise OSError(f"{p}: ABI version {lib.wost_abi_version()}, this binding needs {ABI_VERSION}; "
-                              "rebuild the library")
             _lib = lib
     return _lib
 
@@ -212,6 +218,8 @@ def _scene_desc(spec: dict, device: int, leaf_size: int, keep: list):
     d.g = _field(spec.get("g"), keep)
     d.h = _field(spec.get("h"), keep)
     d.f = _field(spec.get("f"), keep)
+    d.g_minus = _field(spec.get("g_minus"), keep)
+    d.h_minus = _field(spec.get("h_minus"), keep)
     d.device = device
     d.leaf_size = leaf_size
     return d
@@ -256,14 +264,15 @@ def wost_scene_get_info(h) -> dict:
 
 def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
                kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
-               screen_after=0):
+               screen_after=0, stack_depth=0, visit_limit=0):
     """Starts a solve.  `points` is a numpy array (host) or a torch CUDA
     tensor (device); normals/on_neumann likewise.  sigma > 0 solves the
-    screened equation from step screen_after on.  Returns the handle."""
+    screened equation from step screen_after on.  stack_depth / visit_limit
+    (0 = defaults) bound the traversals (guards).  Returns the handle."""
     lib = load()
     keep = []
     d = _solve_desc(keep, points, walks_per_point, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                    normals, on_neumann, stream, sigma, screen_after)
+                    normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit)
     h = C.c_void_p()
     _check(lib.wost_solve(scene, C.byref(d), C.byref(h)))
     return h
@@ -289,7 +298,8 @@ def wost_solve_batch(scenes, requests, stream=None):
 
 class wost_engine_desc(C.Structure):
     _fields_ = [("device", C.c_int32), ("memory_budget_bytes", C.c_int64), ("round_seconds", C.c_double),
-                ("min_walks", C.c_int32), ("max_walks_per_point", C.c_int32), ("block_size", C.c_int32)]
+                ("min_walks", C.c_int32), ("max_walks_per_point", C.c_int32), ("block_size", C.c_int32),
+                ("max_wait_seconds", C.c_double)]
 
 
 class wost_engine_stats(C.Structure):
@@ -301,9 +311,10 @@ class wost_engine_stats(C.Structure):
 
 
 def wost_engine_create(device=0, memory_budget_bytes=0, round_seconds=0.0, min_walks=0, max_walks_per_point=0,
-                       block_size=0):
+                       block_size=0, max_wait_seconds=0.0):
     lib = load()
-    d = wost_engine_desc(device, memory_budget_bytes, round_seconds, min_walks, max_walks_per_point, block_size)
+    d = wost_engine_desc(device, memory_budget_bytes, round_seconds, min_walks, max_walks_per_point, block_size,
+                         max_wait_seconds)
     h = C.c_void_p()
     _check(lib.wost_engine_create(C.byref(d), C.byref(h)))
     return h
@@ -347,10 +358,12 @@ def wost_engine_destroy(engine):
 
 def _solve_desc(keep, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
                 kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
-                screen_after=0):
+                screen_after=0, stack_depth=0, visit_limit=0):
     d = wost_solve_desc()
     d.sigma = float(sigma)
     d.screen_after = int(screen_after)
+    d.stack_depth = int(stack_depth)
+    d.visit_limit = int(visit_limit)
     if isinstance(points, np.ndarray):
         pts = np.ascontiguousarray(points, np.float32)
         keep.append(pts)
@@ -493,10 +506,11 @@ class Scene:
 
 
 def solve(scene: Scene, points, walks, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0, kernel="plain",
-          block_size=0, normals=None, on_neumann=None, stream=None, timeout=-1.0, sigma=0.0, screen_after=0):
+          block_size=0, normals=None, on_neumann=None, stream=None, timeout=-1.0, sigma=0.0, screen_after=0,
+          stack_depth=0, visit_limit=0):
     """Runs a solve to completion; returns a dict of per-point statistics."""
     h = wost_solve(scene.handle, points, walks, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                   normals, on_neumann, stream, sigma, screen_after)
+                   normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit)
     try:
         wost_wait(h, timeout)
         mean, se, wd, prog = wost_poll(h, points.shape[0])
@@ -520,14 +534,31 @@ def wost_solve_static(scene, points, walks_per_point, epsilon, r_min, max_steps,
     they solve.  points (n x dim), mean_out and stderr_out (n) are CUDA
     float32 tensors owned by the caller; the call returns once the work is
     enqueued on `stream`."""
+    info = wost_scene_get_info(scene)
     for name, t in (("points", points), ("mean_out", mean_out), ("stderr_out", stderr_out)):
         if t is not None and not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4
                                   and t.is_contiguous()):
             raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        if t is not None and t.device.index != info["device"]:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the scene on cuda:{info['device']}")
+    # the C entry point takes raw pointers and cannot check sizes itself
+    if points.dim() != 2 or points.shape[1] != info["dim"]:
+        raise ValueError(f"points must be (n, {info['dim']}) for this scene, got {tuple(points.shape)}")
+    n = int(points.shape[0])
+    for name, t in (("mean_out", mean_out), ("stderr_out", stderr_out)):
+        if t is not None and t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} values, fewer than the {n} points")
     _check(load().wost_solve_static(scene, int(points.shape[0]), points.data_ptr(), int(walks_per_point),
                                     float(epsilon), float(r_min), int(max_steps), int(seed), int(first_walk),
                                     mean_out.data_ptr(), None if stderr_out is None else stderr_out.data_ptr(),
                                     _stream_ptr(stream)))
+
+
+def wost_read_probe(buf, passes, sink, stream=None):
+    """One read sweep kernel over a contiguous CUDA tensor `buf` (passes
+    sweeps of 16-byte loads that bypass L1); the caller times it."""
+    _check(load().wost_read_probe(_dptr(buf), int(buf.numel() * buf.element_size()), int(passes), _dptr(sink),
+                                  _stream_ptr(stream)))
 
 
 def wost_screened_kernels(dim, rho, R, sigma, stream=None):

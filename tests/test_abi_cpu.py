@@ -36,7 +36,36 @@ def test_library_exports_every_declared_symbol(lib):
     cdll = C.CDLL(wost.LIBPATH)
     missing = [n for n in declared_functions() if not hasattr(cdll, n)]
     assert not missing, missing
-    assert wost.wost_abi_version() == wost.ABI_VERSION == 2
+    assert wost.wost_abi_version() == wost.ABI_VERSION == 3
+
+
+STRUCTS = ("wost_field", "wost_scene_desc", "wost_scene_info", "wost_solve_desc", "wost_progress",
+           "wost_engine_desc", "wost_engine_stats", "wost_tune_result")
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """sizeof and every offsetof of the public structures, as a C compiler
+    lays them out from include/wost.h, against the binding's ctypes mirrors
+    (the version number alone would not catch a drift between them)."""
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "wost.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(wost, name)
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in STRUCTS:
+        cls = getattr(wost, name)
+        assert got[(name, "sizeof")] == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
 
 
 def _good():
@@ -47,7 +76,7 @@ def _good():
     (lambda s: s.update(dim=4), "dim"),
     (lambda s: s["prims"].__setitem__((3, 1), 999), "index out of range"),
     (lambda s: s["prims"].__setitem__((2, 0), -1), "negative index"),
-    (lambda s: s["flags"].__setitem__(5, 2), "flag"),
+    (lambda s: s["flags"].__setitem__(5, 4), "flag"),
     (lambda s: s["vertices"].__setitem__((1, 0), np.nan), "non-finite"),
     (lambda s: s.update(g={"kind": "per_vertex", "values": None}), "missing values"),
     (lambda s: s.update(g={"kind": "analytic", "fn": "exp_cos", "params": []}, f={"kind": "per_vertex", "values": np.zeros(16)}), "f per vertex"),

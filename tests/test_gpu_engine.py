@@ -2,8 +2,14 @@
 
 Every walk draws Philox numbers keyed by (seed, point, walk, step), so a
 solve gives the same walks whether it runs alone, in a batch or in the
-engine's mix; only the order of the FP64 additions can differ.
+engine's mix.  Between runs of one kernel only the order of the FP64
+additions differs (compared to 1e-9); the batched kernel is a separately
+compiled instantiation (it also serves screened solves), whose single-
+precision arithmetic may round differently in the last bit (fused
+multiply-adds), so against the one-solve kernels walks agree to FP32
+rounding (compared to 1e-6; a different walk would differ by O(1)).
 """
+FP32_WALKS = dict(rtol=1e-6, atol=1e-7)
 import time
 
 import numpy as np
@@ -62,7 +68,7 @@ def test_batch_equals_solves_alone(wost, mix):
             wost.wost_solve_destroy(h)
     for i, (sc, s) in enumerate(zip(specs, S)):
         ref = _alone(wost, s, sc, walks[i], 10 + i)
-        np.testing.assert_allclose(got[i][0], ref["mean"], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(got[i][0], ref["mean"], **FP32_WALKS)
         assert got[i][3]["done"] == 1 and int(got[i][2].sum()) == len(sc["points"]) * walks[i]
 
 
@@ -109,7 +115,7 @@ def test_engine_target_and_cap(wost, mix):
     m, se, w, pr = res[0]
     assert np.all(w == 40)
     ref = _alone(wost, S[0], sc, 40, 5)
-    np.testing.assert_allclose(m, ref["mean"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(m, ref["mean"], **FP32_WALKS)
 
 
 def test_engine_budget_admission_and_rejection(wost, mix):
@@ -159,5 +165,35 @@ def test_engine_cancel_and_progressive_poll(wost, mix):
         assert ei.value.status == wost.ERR_CANCELLED
         wost.wost_solve_destroy(h)
         assert wost.wost_engine_get_stats(eng)["cancelled"] == 1
+    finally:
+        wost.wost_engine_destroy(eng)
+
+
+def test_engine_sheds_requests_that_wait_too_long(wost, mix):
+    """Overload shedding: with memory for one request, a second one queued
+    behind a long-running first is finished with TIMEOUT once it has waited
+    max_wait_seconds for its first walks, and counted as rejected; the first
+    is unaffected."""
+    specs, S = mix
+    sc = specs[0]
+    per_request = len(sc["points"]) * (2 * 4 + 32) + 64
+    eng = wost.wost_engine_create(memory_budget_bytes=int(per_request * 1.5), max_wait_seconds=0.3)
+    try:
+        h1 = wost.wost_engine_submit(eng, S[0].handle, sc["points"], 0.0, 1 << 16, sc["epsilon"], sc["r_min"],
+                                     sc["max_steps"], seed=1)
+        h2 = wost.wost_engine_submit(eng, S[0].handle, sc["points"], 0.0, 32, sc["epsilon"], sc["r_min"],
+                                     sc["max_steps"], seed=2)
+        t0 = time.perf_counter()
+        with pytest.raises(wost.WostError) as ei:
+            wost.wost_wait(h2, 60)
+        assert ei.value.status == wost.ERR_TIMEOUT and time.perf_counter() - t0 < 30
+        st = wost.wost_engine_get_stats(eng)
+        assert st["rejected"] == 1 and st["admitted"] == 1
+        assert wost.wost_poll(h1, len(sc["points"]))[3]["walks_done"] > 0
+        wost.wost_cancel(h1)
+        with pytest.raises(wost.WostError):
+            wost.wost_wait(h1, 120)
+        wost.wost_solve_destroy(h1)
+        wost.wost_solve_destroy(h2)
     finally:
         wost.wost_engine_destroy(eng)

@@ -320,6 +320,82 @@ def test_walk_per_vertex_data_vs_exact_and_oracle(wost, where):
         assert rms_g <= 1.1 * rms_o, (rms_g, rms_o)
 
 
+@pytest.mark.parametrize("where", ["flower_mid", "flower_near_vertex", "sphere_3d"])
+def test_walk_from_points_on_the_neumann_boundary(wost, where):
+    """Evaluation points on the Neumann boundary with their normals (Alg. 1's
+    Require: x0 may lie on the Neumann part): the first step samples the
+    hemisphere about -n_x, starts its queries off the boundary (R4) and
+    weights the Neumann term with alpha = 1/2 (R8).  Against the exact
+    solution and against the oracle on the same random streams."""
+    if where == "sphere_3d":
+        sc = scenes.box_sphere_scene(data="analytic")
+        V, P = sc["vertices"].astype(np.float64), sc["prims"]
+        sel = np.nonzero(sc["flags"] == 1)[0][::37]
+        pts = (V[P[sel, 0]] + V[P[sel, 1]] + V[P[sel, 2]]) / 3.0
+        walks, fn = 2000, "quad3"
+    else:
+        sc = scenes.config1()
+        V, P = sc["vertices"].astype(np.float64), sc["prims"]
+        sel = np.nonzero(sc["flags"] == 1)[0][::4]
+        s = 0.5 if where == "flower_mid" else 0.9
+        pts = V[P[sel, 0]] * (1 - s) + V[P[sel, 1]] * s
+        walks, fn = 3000, "exp_cos"
+    nrm = scenes.prim_normals(sc)[sel]
+    on = np.ones(len(sel), np.uint8)
+    S = wost.Scene(sc)
+    res = wost.solve(S, _dev(pts), walks, 1e-3, 0.0, 1024, seed=41, kernel="persistent",
+                     normals=_dev(nrm), on_neumann=torch.from_numpy(on).cuda())
+    S.close()
+    assert res["guard_flags"] == 0 and res["capped_walks"] == 0
+    ref = oracle.solve(oracle.Scene(sc), pts, walks, 1e-3, max_steps=1024, seed=41, normals=nrm, on_neumann=on,
+                       per_walk=True)
+    u = scenes.exact_u(fn, (), pts)
+    check_z(res["mean"] - u, res["se"], 3e-3, label=f"gpu boundary starts {where}", walks=walks,
+            kurt=kurtosis(ref["per_walk"]))
+    rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
+    rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
+    assert rms_g <= 1.1 * rms_o + 1e-3, (rms_g, rms_o)
+
+
+def _app_b_case(name):
+    rng = np.random.default_rng(60)
+    if name in ("slit", "crack"):
+        sc = scenes.slit_square_scene() if name == "slit" else scenes.crack_square_scene()
+        p = rng.uniform(-0.95, 0.95, (1000, 2))
+        pts = p[(np.abs(p[:, 1]) > 0.05) | (p[:, 0] < -0.05)][:192]
+        return sc, pts, 1e-4, (1.05e-4 / 0.05 if name == "slit" else 1.05e-4 * 3.0), 4096
+    if name == "plate_3d":
+        sc = scenes.plate_cube_scene()
+        p = rng.uniform(-0.85, 0.85, (1000, 3))
+        pts = p[(np.abs(p[:, 2] - 0.1) > 0.04) | (np.abs(p[:, 0]) > 0.55) | (np.abs(p[:, 1]) > 0.55)][:128]
+        return sc, pts, 1e-3, 1.05e-3 * 1.7, 16384
+    sc = scenes.sheet_square_scene(data=name.split(":")[1])
+    p = rng.uniform(-0.9, 0.9, (1000, 2))
+    pts = p[(np.abs(p[:, 1] - 0.1) > 0.03) | (np.abs(p[:, 0]) > 0.55)][:192]
+    return sc, pts, 1e-3, 1.05e-3 * 1.6, 4096
+
+
+@pytest.mark.parametrize("name", ["slit", "crack", "sheet:analytic", "sheet:per_corner", "sheet:per_corner_minus",
+                                  "plate_3d"])
+def test_walk_double_sided_boundaries_vs_exact_and_oracle(wost, name):
+    """App. B: double-sided Dirichlet data on a slit (u = polar angle, 0 above
+    and 2 pi below), a zero-flux Neumann crack across which u jumps, and
+    Neumann sheets / a 3D plate inside Dirichlet boxes with the flux of each
+    side given analytically, per corner, or per corner for both sides.
+    Against the exact solution and the oracle on the same random streams."""
+    sc, pts, eps, allow, cap = _app_b_case(name)
+    pts = pts.astype(np.float32)
+    res = _gpu_solve(wost, sc, pts, 1024, 61, "persistent", eps=eps, max_steps=cap)
+    assert res["guard_flags"] == 0 and res["capped_walks"] == 0
+    ref = oracle.solve(oracle.Scene(sc), pts, 1024, eps, None, cap, seed=61, per_walk=True)
+    u = scenes.exact_u(*sc["exact"], pts)
+    check_z(res["mean"] - u, res["se"], allow, label=f"gpu {name}", walks=1024, kurt=kurtosis(ref["per_walk"]))
+    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.2 * np.median(ref["se"])
+    rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
+    rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
+    assert rms_g <= 1.1 * rms_o + 1e-3, (rms_g, rms_o)
+
+
 def test_plain_and_persistent_give_the_same_walks(wost):
     sc = scenes.config1(n_points=64)
     a = _gpu_solve(wost, sc, sc["points"], 256, 9, "plain")
@@ -415,6 +491,50 @@ def test_edge_cases(wost):
             wost.wost_solve(S.handle, _dev(sc["points"]), kw.get("walks", 4), kw.get("eps", 1e-3),
                             kw.get("rmin", 0.0), kw.get("steps", 16))
         assert ei.value.status == wost.ERR_INVALID_ARG
+    S.close()
+
+
+@pytest.mark.parametrize("kernel", ["plain", "persistent", "resumable"])
+@pytest.mark.parametrize("knob, bit", [("stack_depth", 1), ("visit_limit", 2)])
+def test_device_guards_fire_and_are_reported(wost, kernel, knob, bit):
+    """A traversal stack of 2 entries (the scene's trees are 13-15 deep) or
+    a limit of 3 node visits per traversal: the bounded device guards stop
+    the traversal, record their bit, and wost_wait / wost_poll return
+    INTERNAL promptly (a limit running out, no fault)."""
+    import time
+    sc = SCENES["koch3"]
+    S = wost.Scene(sc)
+    assert S.info()["stack_depth"] > 4
+    pts = _dev(sc["points"][:64])
+    h = wost.wost_solve(S.handle, pts, 16, sc["epsilon"], sc["r_min"], 256, seed=3, kernel=kernel,
+                        **{knob: 2 if knob == "stack_depth" else 3})
+    t0 = time.perf_counter()
+    with pytest.raises(wost.WostError) as ei:
+        wost.wost_wait(h, 120.0)
+    assert ei.value.status == wost.ERR_INTERNAL
+    assert time.perf_counter() - t0 < 60
+    with pytest.raises(wost.WostError) as ei:
+        wost.wost_poll(h, 64)
+    assert ei.value.status == wost.ERR_INTERNAL
+    wost.wost_solve_destroy(h)
+    # the same solve with the defaults: no guard
+    r = wost.solve(S, pts, 16, sc["epsilon"], sc["r_min"], 256, seed=3, kernel=kernel)
+    assert r["guard_flags"] == 0
+    S.close()
+
+
+def test_autotune_picks_a_tried_block_and_keeps_the_walks(wost):
+    sc = scenes.config2(grid=32, level=3)
+    S = wost.Scene(sc)
+    pts = _dev(sc["points"])
+    before = wost.solve(S, pts, 32, sc["epsilon"], sc["r_min"], 4096, seed=8, kernel="persistent")
+    t = wost.wost_scene_autotune(S.handle, pts, 16, sc["epsilon"], sc["r_min"], 4096)
+    assert t["block_size"] in t["tried"] and len(t["tried"]) >= 2
+    assert t["steps_per_second"] == max(t["tried"].values()) > 0
+    after = wost.solve(S, pts, 32, sc["epsilon"], sc["r_min"], 4096, seed=8, kernel="persistent")
+    # the tuned launch shape runs the same walks
+    np.testing.assert_allclose(after["mean"], before["mean"], rtol=1e-9, atol=1e-12)
+    assert after["total_steps"] == before["total_steps"]
     S.close()
 
 

@@ -277,9 +277,9 @@ def test_q4_measure_of_plate_in_ball_3d():
 # ---------------------------------------------------------------------------
 # the walk (Alg. 1) against exact solutions
 # ---------------------------------------------------------------------------
-def _check_exact(sc, pts, walks, eps, seed=7, z=4.0, r_min=None, chi2=True):
+def _check_exact(sc, pts, walks, eps, seed=7, z=4.0, r_min=None, chi2=True, max_steps=1024):
     S = oracle.Scene(sc)
-    res = oracle.solve(S, pts, walks, eps, r_min, 1024, seed=seed, per_walk=True)
+    res = oracle.solve(S, pts, walks, eps, r_min, max_steps, seed=seed, per_walk=True)
     fn, pr = sc["exact"]
     u = scenes.exact_u(fn, pr, pts)
     # epsilon-shell bias bound: |u(xbar) - u(x)| <= eps * max|grad u|
@@ -404,6 +404,70 @@ def test_walk_per_vertex_data_exact_for_linear_u_3d():
     sc = scenes.cube_scene(4, fn="linear", params=(0.2, 0.5, -0.3, 0.8), neumann_faces=(5,), data="per_vertex")
     rng = np.random.default_rng(33)
     _check_exact(sc, rng.uniform(-0.85, 0.85, (32, 3)).astype(np.float32), 1024, 1e-3)
+
+
+# ---------------------------------------------------------------------------
+# double-sided boundaries (App. B)
+# ---------------------------------------------------------------------------
+def _slit_points(rng, n):
+    p = rng.uniform(-0.95, 0.95, (4 * n, 2))
+    keep = (np.abs(p[:, 1]) > 0.05) | (p[:, 0] < -0.05)
+    return p[keep][:n].astype(np.float32)
+
+
+def test_walk_double_sided_dirichlet_slit():
+    """App. B, double-sided Dirichlet data: the square with a slit from the
+    centre to the right side, u = polar angle in [0, 2 pi): 0 on the slit's
+    upper side, 2 pi on its lower side.  A walk ending at the slit must take
+    the data of the side it is on; the wrong side is off by 2 pi."""
+    sc = scenes.slit_square_scene()
+    rng = np.random.default_rng(51)
+    pts = _slit_points(rng, 64)
+    S = oracle.Scene(sc)
+    res = oracle.solve(S, pts, 1024, 1e-4, None, 1024, seed=5, per_walk=True)
+    u = scenes.exact_u("polar_angle", (), pts)
+    # shell bias: |grad u| = 1/rho is large only near the slit's tip
+    check_z(res["mean"] - u, res["se"], 1e-4 * 1.05 / 0.05, walks=1024, kurt=kurtosis(res["per_walk"]))
+
+
+def test_walk_double_sided_neumann_crack():
+    """App. B at a Neumann crack: the square with a zero-flux crack from the
+    centre to the right side, u = sqrt(rho) cos(theta/2), which jumps by
+    2 sqrt(rho) across the crack.  A walk that hits the crack must leave on
+    the side it came from; one that crossed would carry the other side's
+    value (the rule that keeps it on its side is checked by planting it
+    out of the oracle)."""
+    sc = scenes.crack_square_scene()
+    rng = np.random.default_rng(54)
+    pts = _slit_points(rng, 64)
+    S = oracle.Scene(sc)
+    res = oracle.solve(S, pts, 1024, 1e-4, None, 4096, seed=6, per_walk=True)
+    assert res["capped"].sum() == 0
+    u = scenes.exact_u("crack_mode", (), pts)
+    # |grad u| = 1 / (2 sqrt(rho)), large only next to the tip
+    check_z(res["mean"] - u, res["se"], 1e-4 * 1.05 * 3.0, walks=1024, kurt=kurtosis(res["per_walk"]))
+
+
+@pytest.mark.parametrize("data", ["analytic", "per_corner", "per_corner_minus"])
+def test_walk_double_sided_neumann_sheet_2d(data):
+    """App. B, double-sided Neumann data: a Neumann sheet inside a Dirichlet
+    square, u linear with du/dy = 1.5 across the sheet: h+ = -1.5 on the
+    upper (+) side, h- = +1.5 below.  Sheet hits must keep the walk on its
+    side and Neumann samples must use the data of the side facing the walk;
+    either mistake biases the means by many SE."""
+    sc = scenes.sheet_square_scene(data=data)
+    rng = np.random.default_rng(52)
+    p = rng.uniform(-0.9, 0.9, (400, 2))
+    pts = p[(np.abs(p[:, 1] - 0.1) > 0.03) | (np.abs(p[:, 0]) > 0.55)][:64].astype(np.float32)
+    _check_exact(sc, pts, 1024, 1e-3)
+
+
+def test_walk_double_sided_neumann_plate_3d():
+    sc = scenes.plate_cube_scene()
+    rng = np.random.default_rng(53)
+    p = rng.uniform(-0.85, 0.85, (400, 3))
+    pts = p[(np.abs(p[:, 2] - 0.1) > 0.04) | (np.abs(p[:, 0]) > 0.55) | (np.abs(p[:, 1]) > 0.55)][:48]
+    _check_exact(sc, pts.astype(np.float32), 1024, 1e-3, max_steps=16384)
 
 
 def test_walk_3d_cube_around_neumann_sphere():

@@ -69,3 +69,22 @@ def test_static_rejects_too_many_points_and_allocates_nothing(wost):
     assert torch.cuda.mem_get_info()[0] == free0
     assert bool(torch.isfinite(mean).all())
     S.close()
+
+
+def test_static_binding_rejects_mismatched_arrays(wost):
+    """The C entry point takes raw pointers and cannot check sizes: the
+    binding checks the points' shape against the scene's dimension and the
+    output lengths against the point count before it calls."""
+    sc = scenes.config1()
+    S = wost.Scene(sc)
+    pts3 = torch.zeros((16, 3), dtype=torch.float32, device="cuda")
+    out = torch.empty(16, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError, match="points must be"):
+        wost.wost_solve_static(S.handle, pts3, 4, 1e-3, 1e-3, 64, 1, 0, out, None)
+    pts = torch.zeros((16, 2), dtype=torch.float32, device="cuda")
+    short = torch.empty(15, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError, match="fewer than"):
+        wost.wost_solve_static(S.handle, pts, 4, 1e-3, 1e-3, 64, 1, 0, short, None)
+    with pytest.raises(ValueError, match="fewer than"):
+        wost.wost_solve_static(S.handle, pts, 4, 1e-3, 1e-3, 64, 1, 0, out, short)
+    S.close()
