@@ -136,16 +136,18 @@ typedef struct {
     int64_t device_bytes;      /* bytes of resident scene data               */
     double build_seconds;
     float bbox_lo[3], bbox_hi[3];
-    /* layout the walk kernels traverse: lanes per walk (1: binary trees, one
-     * lane per walk; 8: 8-wide trees, 8 cooperating lanes per walk), bytes
-     * read per node visit (node record; the silhouette tree adds its child
-     * cones), and the wide trees' node counts and depths */
+    /* layout the walk kernels traverse by default (the scene's tuned choice,
+     * else binary): lanes per walk (1: binary trees, one lane per walk; 8:
+     * 8-wide trees, 8 cooperating lanes per walk), bytes read per node visit
+     * (node record; the silhouette tree adds its child cones), and the wide
+     * trees' node counts and depths */
     int32_t lanes_per_walk;
     int32_t node_bytes, cone_bytes;
     int64_t wide_nodes_dirichlet, wide_nodes_neumann, wide_nodes_silhouette;
     int32_t wide_depth_dirichlet, wide_depth_neumann, wide_depth_silhouette;
     int32_t device;            /* CUDA device ordinal the scene lives on       */
-    int32_t stack_depth;       /* traversal stack entries per walk it needs    */
+    int32_t stack_depth;       /* traversal stack entries per walk (per team)
+                                  of that layout                               */
 } wost_scene_info;
 
 /* Builds the hierarchies on the host, uploads them, returns a handle.
@@ -222,6 +224,11 @@ typedef struct {
                                   the tree's nodes plus 8 (more than a correct
                                   traversal makes).  A traversal that reaches
                                   the limit stops and sets guard bit 2        */
+    int32_t lanes_per_walk;    /* 1: one lane per walk over the binary trees;
+                                  8: a team of 8 lanes per walk over the 8-wide
+                                  trees (persistent and resumable Poisson
+                                  solves); 0: the scene's choice (set by
+                                  wost_scene_autotune, else 1)               */
 } wost_solve_desc;
 
 typedef struct {
@@ -446,12 +453,18 @@ typedef struct {
     int32_t n_tried;
     int32_t tried_block[8];
     double tried_steps_per_second[8];
+    int32_t lanes_per_walk;     /* fastest layout: 1 (binary) or 8 (8-wide teams) */
+    int32_t tried_lanes[8];
 } wost_tune_result;
 
 /* Times the persistent kernel on a sample of the caller's points (device
- * pointer, n points, at most 8192 used) for block sizes 64..256 and keeps
- * the fastest as the scene's default for persistent, batched and engine
- * launches whose block_size is 0.  Same validation as wost_solve. */
+ * pointer, n points, at most 8192 used) for each layout -- one lane per walk
+ * over the binary trees, 8-lane teams over the 8-wide trees -- and block
+ * sizes 64..256 (8 combinations), and keeps the fastest block size as the
+ * scene's default for persistent, batched and engine launches whose
+ * block_size is 0, and the fastest layout as its default for persistent and
+ * resumable Poisson solves whose lanes_per_walk is 0 (wost_scene_info then
+ * reports that layout).  Same validation as wost_solve. */
 wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t n, int32_t walks_per_point,
                                 float epsilon, float r_min, int32_t max_steps, wost_tune_result *out);
 

@@ -77,8 +77,10 @@ struct wost_scene {
     unsigned int *guard = nullptr;        // device guard word for query kernels
     wost::SceneView *view_dev = nullptr;  // device copy of `view` (batched launches)
     wost_scene_info info{};
-    int stack_depth = 0;
+    int stack_depth = 0;                  // traversal stack entries per walk, one lane per walk
+    int stack_depth_team = 0;             // ... per 8-lane team over the 8-wide trees
     int tuned_block = 0;                  // set by wost_scene_autotune (0 = not tuned)
+    int tuned_lanes = 1;                  // lanes per walk chosen by wost_scene_autotune
     std::mutex mu;
     ~wost_scene() {
         if (guard) cudaFree(guard);
@@ -93,6 +95,7 @@ struct wost_solve_handle {
     int64_t n_points = 0;
     int32_t walks = 0;
     int block = 128;
+    int lanes = 1;                        // lanes per walk (persistent / resumable kernels)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t poll_stream = nullptr;
@@ -132,6 +135,8 @@ struct wost_solve_handle {
 };
 
 namespace wost {
+// Layout fields of a scene's info for `lanes` lanes per walk.
+void set_layout_info(wost_scene *s, int lanes);
 // Validates a solve description, allocates and fills the solve's device
 // buffers on `stream`, fills h->sp and h->acc.  Does not launch.
 wost_status prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream, wost_solve_handle *h);

@@ -123,14 +123,11 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
             }
             s->view.rmax = std::sqrt(d2);
         }
-#if WOST_TEAM == 1
         // binary trees: one pending subtree per level
         s->stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
-#else
         // 8-wide trees: at most 7 pending subtrees per level; odd, so that
         // the teams of a warp start in different shared-memory banks
-        s->stack_depth = ((WOST_WIDE - 1) * std::max(H.D.wdepth, std::max(H.N.wdepth, H.S.wdepth)) + 1) | 1;
-#endif
+        s->stack_depth_team = ((WOST_WIDE - 1) * std::max(H.D.wdepth, std::max(H.N.wdepth, H.S.wdepth)) + 1) | 1;
         CK(cudaMalloc(&s->view_dev, sizeof(SceneView)), "cudaMalloc view");
         CK(cudaMemcpy(s->view_dev, &s->view, sizeof(SceneView), cudaMemcpyHostToDevice), "copy view");
         wost_scene_info &I = s->info;
@@ -145,9 +142,6 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         I.depth_dirichlet = H.D.depth;
         I.depth_neumann = H.N.depth;
         I.depth_silhouette = H.S.depth;
-        I.lanes_per_walk = WOST_TEAM;
-        I.node_bytes = WOST_TEAM == 1 ? (H.dim == 2 ? 48 : 64) : 2 * WOST_WIDE * 16;
-        I.cone_bytes = WOST_TEAM == 1 ? 32 : WOST_WIDE * 16;
         I.wide_nodes_dirichlet = H.D.wn_nodes;
         I.wide_nodes_neumann = H.N.wn_nodes;
         I.wide_nodes_silhouette = H.S.wn_nodes;
@@ -157,7 +151,7 @@ wost_status wost_scene_create(const wost_scene_desc *desc, wost_scene **out) {
         I.device_bytes = bytes;
         I.build_seconds = H.build_seconds;
         I.device = s->device;
-        I.stack_depth = s->stack_depth;
+        set_layout_info(s.get(), 1);
         for (int a = 0; a < 3; ++a) {
             I.bbox_lo[a] = H.lo[a];
             I.bbox_hi[a] = H.hi[a];
@@ -191,7 +185,7 @@ wost_status wost_scene_validate(const wost_scene_desc *desc, wost_scene_info *ou
         I.depth_dirichlet = H.D.depth;
         I.depth_neumann = H.N.depth;
         I.depth_silhouette = H.S.depth;
-        I.lanes_per_walk = WOST_TEAM;
+        I.lanes_per_walk = 1;
         I.wide_nodes_dirichlet = H.D.wn_nodes;
         I.wide_nodes_neumann = H.N.wn_nodes;
         I.wide_nodes_silhouette = H.S.wn_nodes;
@@ -200,11 +194,9 @@ wost_status wost_scene_validate(const wost_scene_desc *desc, wost_scene_info *ou
         I.wide_depth_silhouette = H.S.wdepth;
         I.build_seconds = H.build_seconds;
         I.device = desc->device;
-#if WOST_TEAM == 1
         I.stack_depth = std::max(H.D.depth, std::max(H.N.depth, H.S.depth)) + 2;
-#else
-        I.stack_depth = ((WOST_WIDE - 1) * std::max(H.D.wdepth, std::max(H.N.wdepth, H.S.wdepth)) + 1) | 1;
-#endif
+        I.node_bytes = H.dim == 2 ? 48 : 64;
+        I.cone_bytes = 32;
         for (int a = 0; a < 3; ++a) {
             I.bbox_lo[a] = H.lo[a];
             I.bbox_hi[a] = H.hi[a];
@@ -232,6 +224,14 @@ wost_status wost_scene_get_info(const wost_scene *scene, wost_scene_info *out) {
 }
 
 }  // extern "C"
+
+void wost::set_layout_info(wost_scene *s, int lanes) {
+    wost_scene_info &I = s->info;
+    I.lanes_per_walk = lanes;
+    I.node_bytes = lanes == 1 ? (s->host.dim == 2 ? 48 : 64) : 2 * WOST_WIDE * 16;
+    I.cone_bytes = lanes == 1 ? 32 : WOST_WIDE * 16;
+    I.stack_depth = lanes == 1 ? s->stack_depth : s->stack_depth_team;
+}
 
 // Validates a solve description, allocates and fills the solve's device
 // buffers on `stream`, and fills h->sp / h->acc.  Does not launch.
@@ -261,6 +261,14 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     int block = d->block_size ? d->block_size : (scene->tuned_block ? scene->tuned_block : 128);
     if (block < 32 || block > 256 || block % 32)
         return fail(WOST_ERR_INVALID_ARG, "block_size must be 32..256, multiple of 32");
+    if (d->lanes_per_walk != 0 && d->lanes_per_walk != 1 && d->lanes_per_walk != WOST_WIDE)
+        return fail(WOST_ERR_INVALID_ARG, "lanes_per_walk must be 0, 1 or 8");
+    // 8-lane teams: persistent and resumable Poisson solves only; the tuned
+    // choice applies where it can, an explicit request elsewhere is an error
+    const bool team_ok = (d->kernel == WOST_KERNEL_PERSISTENT || d->kernel == WOST_KERNEL_RESUMABLE) && !(d->sigma > 0);
+    if (d->lanes_per_walk == WOST_WIDE && !team_ok)
+        return fail(WOST_ERR_INVALID_ARG, "8 lanes per walk: persistent or resumable Poisson solves only");
+    const int lanes = d->lanes_per_walk ? d->lanes_per_walk : (team_ok ? scene->tuned_lanes : 1);
     CK(cudaSetDevice(scene->device), "cudaSetDevice");
     h->scene = scene;
     h->device = scene->device;
@@ -269,6 +277,7 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     h->walks = d->walks_per_point;
     h->kernel = d->kernel;
     h->block = block;
+    h->lanes = lanes;
     h->stream = stream;
     const int dim = h->dim;
     CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -312,7 +321,7 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     sp.key1 = (uint32_t)(d->seed >> 32);
     sp.offset = 1e-6f;
     sp.vis_tmax = 1.f - 1e-4f;
-    sp.stack_depth = d->stack_depth ? d->stack_depth : scene->stack_depth;
+    sp.stack_depth = d->stack_depth ? d->stack_depth : (lanes == 1 ? scene->stack_depth : scene->stack_depth_team);
     sp.visit_limit = (uint32_t)d->visit_limit;
     sp.sigma = d->sigma;
     sp.sqrt_sigma = std::sqrt(d->sigma);
@@ -363,8 +372,9 @@ wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_h
         h->own_events = true;
         if (d->kernel == WOST_KERNEL_RESUMABLE) {
             // state only; the launches come from wost_solve_advance
-            CK(resume_grid(h->dim, h->block, h->sp.stack_depth, &h->resume_blocks), "occupancy");
-            CK(h->slots.alloc((size_t)resume_slots(h->block, h->resume_blocks) * 3 * sizeof(float4)), "cudaMalloc slots");
+            CK(resume_grid(h->dim, h->block, h->sp.stack_depth, &h->resume_blocks, h->lanes), "occupancy");
+            CK(h->slots.alloc((size_t)resume_slots(h->block, h->resume_blocks, h->lanes) * 3 * sizeof(float4)),
+               "cudaMalloc slots");
             CK(h->rstate.alloc(16), "cudaMalloc counters");
             CK(cudaMemsetAsync(h->slots.p, 0, h->slots.bytes, stream), "memset");
             CK(cudaMemsetAsync(h->rstate.p, 0, 16, stream), "memset");
@@ -387,8 +397,8 @@ wost_status wost_solve(wost_scene *scene, const wost_solve_desc *d, wost_solve_h
                 le = launch_walk_count(scene->view, sp, acc, (unsigned long long *)h->counts.p, h->block, stream);
         } else {
             int blocks = 0;
-            le = persistent_grid(h->dim, h->block, sp.stack_depth, &blocks);
-            if (le == cudaSuccess) le = launch_walk_persistent(scene->view, sp, acc, h->block, blocks, stream);
+            le = persistent_grid(h->dim, h->block, sp.stack_depth, &blocks, h->lanes);
+            if (le == cudaSuccess) le = launch_walk_persistent(scene->view, sp, acc, h->block, blocks, stream, h->lanes);
         }
         if (le != cudaSuccess) return cuda_fail(le, "kernel launch");
         CK(cudaEventRecord(h->ev_done, stream), "cudaEventRecord");
@@ -606,7 +616,8 @@ static wost_status advance_locked(wost_solve_handle *h, int iters, cudaStream_t 
     unsigned int *live = (unsigned int *)((char *)h->rstate.p + 8);
     CK(cudaMemsetAsync(live, 0, sizeof(unsigned int), s), "memset");
     ResumeState rs{(float4 *)h->slots.p, (unsigned long long *)h->rstate.p, live};
-    CK(launch_walk_resume(h->scene->view, h->sp, h->acc, rs, iters, h->block, h->resume_blocks, s), "kernel launch");
+    CK(launch_walk_resume(h->scene->view, h->sp, h->acc, rs, iters, h->block, h->resume_blocks, s, h->lanes),
+       "kernel launch");
     CK(cudaEventRecord(h->ev_done, s), "cudaEventRecord");
     h->launches++;
     return WOST_OK;
@@ -775,8 +786,10 @@ wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t 
         const int64_t m = std::min<int64_t>(n, 8192);
         const int blocks[4] = {64, 128, 192, 256};
         double best = -1;
-        for (int bi = 0; bi < 4; ++bi) {
+        for (int ci = 0; ci < 8; ++ci) {
+            const int bi = ci % 4, lanes = ci < 4 ? 1 : WOST_WIDE;
             wost_solve_desc d{};
+            d.lanes_per_walk = lanes;
             d.n_points = m;
             d.points = points;
             d.memory = WOST_MEM_DEVICE;
@@ -800,15 +813,19 @@ wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t 
                 rate = pr.elapsed_seconds > 0 ? (double)pr.total_steps / pr.elapsed_seconds : 0;
             }
             out->tried_block[out->n_tried] = blocks[bi];
+            out->tried_lanes[out->n_tried] = lanes;
             out->tried_steps_per_second[out->n_tried] = rate;
             out->n_tried++;
             if (rate > best) {
                 best = rate;
                 out->block_size = blocks[bi];
+                out->lanes_per_walk = lanes;
                 out->steps_per_second = rate;
             }
         }
         scene->tuned_block = out->block_size;
+        scene->tuned_lanes = out->lanes_per_walk;
+        set_layout_info(scene, scene->tuned_lanes);
         return WOST_OK;
     } catch (const std::exception &e) {
         return fail(WOST_ERR_INTERNAL, e.what());

@@ -36,11 +36,6 @@
 #define WOST_MAX_LEAF 16
 #define WOST_MAX_DEPTH 60
 #define WOST_WIDE 8  // children per node of the wide layout (= lanes per walk team)
-// Lanes that cooperate on one walk: 1 = one lane per walk over the binary
-// trees, 8 = a team of 8 lanes per walk over the 8-wide trees.
-#ifndef WOST_TEAM
-#define WOST_TEAM 1
-#endif
 
 namespace wost {
 

@@ -69,11 +69,11 @@ __global__ void k_query_closest(const SceneView sc, int64_t n, const float *pts,
                                 int32_t *prim, int depth, unsigned int *guard) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(depth, guard, cnt);
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     P3 x = load_point<D>(pts, i);
     Closest c = q.closest(sc.D, x, INFINITY);
-    if (!make_team().leader()) return;
+    if (!make_team<1>().leader()) return;
     dist[i] = sqrtf(c.d2);
     closest[D * i] = c.p.x;
     closest[D * i + 1] = c.p.y;
@@ -86,10 +86,10 @@ __global__ void k_query_silhouette(const SceneView sc, int64_t n, const float *p
                                    int depth, unsigned int *guard) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(depth, guard, cnt);
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float d = q.silhouette(sc.S, load_point<D>(pts, i), rmax[i]);
-    if (make_team().leader()) dist[i] = d;
+    if (make_team<1>().leader()) dist[i] = d;
 }
 
 template <int D>
@@ -98,13 +98,13 @@ __global__ void k_query_ray(const SceneView sc, int64_t n, const float *o, const
                             int32_t *prim, int depth, unsigned int *guard) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(depth, guard, cnt);
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int sk = -1;
     if (skip && skip[i] >= 0 && skip[i] < n_ids) sk = rec_of_id[skip[i]];
     float tt;
     int r = q.ray(sc.N, load_point<D>(o, i), load_point<D>(v, i), tmax[i], sk, false, tt);
-    if (!make_team().leader()) return;
+    if (!make_team<1>().leader()) return;
     hit[i] = r >= 0;
     t[i] = r >= 0 ? tt : tmax[i];
     prim[i] = r >= 0 ? __ldg(sc.N.ids + r) : -1;
@@ -115,12 +115,12 @@ __global__ void k_query_sample(const SceneView sc, int64_t n, const float *pts, 
                                uint32_t k1, uint32_t c1, uint32_t c2, float *z, float *pdf, int32_t *prim) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(0, nullptr, cnt);  // Q.4 keeps no stack
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     Stream rng;
     rng.init(k0, k1, (uint32_t)i, c1, c2);
     NSample s = q.sample(sc.N, load_point<D>(pts, i), r[i], rng);
-    if (!make_team().leader()) return;
+    if (!make_team<1>().leader()) return;
     z[D * i] = s.z.x;
     z[D * i + 1] = s.z.y;
     if (D == 3) z[D * i + 2] = s.z.z;
@@ -144,28 +144,36 @@ cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const 
 // The grids of the persistent kernels are sized for the Poisson
 // instantiation; the screened one runs under the same register cap and
 // shared memory, so the same number of its blocks is resident.
-cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out) {
-    return resident_grid(dim == 2 ? (const void *)k_walk_persistent<2, false> : (const void *)k_walk_persistent<3, false>,
+// lanes = 8: the team form over the 8-wide trees (Poisson only; the
+// screened solves and the other kernels use one lane per walk)
+cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out, int lanes) {
+    if (lanes == WOST_WIDE) return persistent_grid_team(dim, block, depth, blocks_out);
+    return resident_grid(dim == 2 ? (const void *)k_walk_persistent<2, false, 1>
+                                  : (const void *)k_walk_persistent<3, false, 1>,
                          block, depth, blocks_out);
 }
 
 cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
-                                   int blocks, cudaStream_t s) {
+                                   int blocks, cudaStream_t s, int lanes) {
     if (sp.sigma > 0.f) return launch_walk_persistent_scr(sc, sp, acc, block, blocks, s);
-    return walk_persistent_launch<false>(sc, sp, acc, block, blocks, s);
+    if (lanes == WOST_WIDE) return launch_walk_persistent_team(sc, sp, acc, block, blocks, s);
+    return walk_persistent_launch<false, 1>(sc, sp, acc, block, blocks, s);
 }
 
-cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out) {
-    return resident_grid(dim == 2 ? (const void *)k_walk_resume<2, false> : (const void *)k_walk_resume<3, false>,
+// the resumable kernels share the persistent ones' occupancy (same body)
+cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out, int lanes) {
+    if (lanes == WOST_WIDE) return persistent_grid_team(dim, block, depth, blocks_out);
+    return resident_grid(dim == 2 ? (const void *)k_walk_resume<2, false, 1> : (const void *)k_walk_resume<3, false, 1>,
                          block, depth, blocks_out);
 }
 
-int64_t resume_slots(int block, int blocks) { return (int64_t)blocks * (block / WOST_TEAM); }
+int64_t resume_slots(int block, int blocks, int lanes) { return (int64_t)blocks * (block / lanes); }
 
 cudaError_t launch_walk_resume(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
-                               const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
+                               const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s, int lanes) {
     if (sp.sigma > 0.f) return launch_walk_resume_scr(sc, sp, acc, rs, iters, block, blocks, s);
-    return walk_resume_launch<false>(sc, sp, acc, rs, iters, block, blocks, s);
+    if (lanes == WOST_WIDE) return launch_walk_resume_team(sc, sp, acc, rs, iters, block, blocks, s);
+    return walk_resume_launch<false, 1>(sc, sp, acc, rs, iters, block, blocks, s);
 }
 
 static cudaError_t query_smem(const void *fn, size_t bytes) {
@@ -176,7 +184,7 @@ static cudaError_t query_smem(const void *fn, size_t bytes) {
 cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pts, float *dist, float *closest,
                                  int32_t *prim, int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
+    unsigned grid = (unsigned)((n + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_closest<2>, sm);
@@ -193,7 +201,7 @@ cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pt
 cudaError_t launch_query_silhouette(const SceneView &sc, int64_t n, const float *pts, const float *rmax, float *dist,
                                     int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
+    unsigned grid = (unsigned)((n + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_silhouette<2>, sm);
@@ -211,7 +219,7 @@ cudaError_t launch_query_ray(const SceneView &sc, int64_t n, const float *o, con
                              const int32_t *skip, const int32_t *rec_of_id, int64_t n_ids, int32_t *hit, float *t,
                              int32_t *prim, int depth, unsigned int *guard, cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
+    unsigned grid = (unsigned)((n + block - 1) / block);
     size_t sm = smem_bytes(depth, block);
     if (sc.dim == 2) {
         cudaError_t e = query_smem((const void *)k_query_ray<2>, sm);
@@ -229,7 +237,7 @@ cudaError_t launch_query_sample(const SceneView &sc, int64_t n, const float *pts
                                 uint32_t k1, uint32_t c1, uint32_t c2, float *z, float *pdf, int32_t *prim,
                                 cudaStream_t s) {
     const int block = 128;
-    unsigned grid = (unsigned)((n * WOST_TEAM + block - 1) / block);
+    unsigned grid = (unsigned)((n + block - 1) / block);
     if (sc.dim == 2)
         k_query_sample<2><<<grid, block, 0, s>>>(sc, n, pts, r, k0, k1, c1, c2, z, pdf, prim);
     else

@@ -11,7 +11,7 @@ cudaError_t launch_walk_plain(const SceneView &sc, const SolveParams &sp, const 
                               cudaStream_t s);
 cudaError_t launch_walk_count(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                               unsigned long long *stats, int block, cudaStream_t s);
-cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out);
+cudaError_t persistent_grid(int dim, int block, int depth, int *blocks_out, int lanes = 1);
 cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out);
 cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_points, unsigned int *max_var_bits,
                                  unsigned long long *min_walks, unsigned long long *steps_sum,
@@ -19,13 +19,16 @@ cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_po
 cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
                               unsigned int *guard, int depth, const int *cancel, int block, int blocks,
                               cudaStream_t s);
+// lanes: lanes per walk, 1 (binary trees) or 8 (8-lane teams over the 8-wide
+// trees; Poisson solves)
 cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
-                                   int blocks, cudaStream_t s);
+                                   int blocks, cudaStream_t s, int lanes = 1);
 // resumable solves: grid of the fixed launch, its walk slots, one launch
-cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out);
-int64_t resume_slots(int block, int blocks);
+cudaError_t resume_grid(int dim, int block, int depth, int *blocks_out, int lanes = 1);
+int64_t resume_slots(int block, int blocks, int lanes = 1);
 cudaError_t launch_walk_resume(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
-                               const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s);
+                               const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s,
+                               int lanes = 1);
 cudaError_t launch_screened_kernels(int dim, int64_t n, const float *rho, const float *R, float sigma, float *G,
                                     float *Q, cudaStream_t s);
 cudaError_t launch_query_closest(const SceneView &sc, int64_t n, const float *pts, float *dist, float *closest,

@@ -43,11 +43,11 @@ cudaError_t launch_walk_count_scr(const SceneView &sc, const SolveParams &sp, co
 }
 cudaError_t launch_walk_persistent_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                        int block, int blocks, cudaStream_t s) {
-    return walk_persistent_launch<true>(sc, sp, acc, block, blocks, s);
+    return walk_persistent_launch<true, 1>(sc, sp, acc, block, blocks, s);
 }
 cudaError_t launch_walk_resume_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                    const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
-    return walk_resume_launch<true>(sc, sp, acc, rs, iters, block, blocks, s);
+    return walk_resume_launch<true, 1>(sc, sp, acc, rs, iters, block, blocks, s);
 }
 
 cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {

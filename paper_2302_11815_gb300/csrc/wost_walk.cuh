@@ -4,9 +4,11 @@
 // screened instantiations and the Bessel functions out of the Poisson
 // module keeps that module's code as compact as before they existed.
 //
-// A walk is carried by a team of WOST_TEAM lanes (1: a lane per walk over
-// the binary trees; 8: a team per walk over the 8-wide trees, see
-// wost_group.cuh).  All lanes of a team hold the same walk state.
+// A walk is carried by a team of T lanes (1: a lane per walk over the binary
+// trees; 8: a team per walk over the 8-wide trees, see wost_group.cuh).  All
+// lanes of a team hold the same walk state.  The persistent and resumable
+// kernels come in both forms, chosen at run time (the autotuner picks one per
+// scene); the other kernels use one lane per walk.
 //
 //   k_walk_plain       one team per walk, one launch per solve; a warp holds
 //                      its teams until its longest walk ends.
@@ -49,37 +51,40 @@
 
 namespace wost {
 
-static_assert(WOST_TEAM == 1 || WOST_TEAM == WOST_WIDE, "a team is one lane or one lane per wide child");
-
+template <int T>
 __device__ __forceinline__ Group make_team() {
+    static_assert(T == 1 || T == WOST_WIDE, "a team is one lane or one lane per wide child");
     Group g;
     int lane = threadIdx.x & 31;
-    g.gl = lane & (WOST_TEAM - 1);
+    g.gl = lane & (T - 1);
     g.base = lane - g.gl;
-    g.mask = ((1u << WOST_TEAM) - 1u) << g.base;
+    g.mask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << g.base;
     return g;
 }
 
-#if WOST_TEAM == 1
+template <int D, bool CN, int T>
+struct PolicyOf;
 template <int D, bool CN>
-using WalkQ = LaneQ<D, CN>;
-#else
+struct PolicyOf<D, CN, 1> {
+    using type = LaneQ<D, CN>;
+};
 template <int D, bool CN>
-using WalkQ = GroupQ<D, CN>;
-#endif
+struct PolicyOf<D, CN, WOST_WIDE> {
+    using type = GroupQ<D, CN>;
+};
 
 // the query policy of this thread's team, with its shared-memory stack
-template <int D, bool CN>
-__device__ __forceinline__ WalkQ<D, CN> make_q(int depth, unsigned int *guard, Cnt<CN> &cnt,
-                                               uint32_t visit_limit = 0u) {
+template <int D, bool CN, int T = 1>
+__device__ __forceinline__ typename PolicyOf<D, CN, T>::type make_q(int depth, unsigned int *guard, Cnt<CN> &cnt,
+                                                                    uint32_t visit_limit = 0u) {
     extern __shared__ int2 smem_stack[];
-#if WOST_TEAM == 1
-    Stack s{smem_stack + threadIdx.x, (int)blockDim.x, depth, guard, visit_limit};
-    return LaneQ<D, CN>{s, cnt};
-#else
-    GStack s{smem_stack + (threadIdx.x / WOST_TEAM) * depth, depth, guard};
-    return GroupQ<D, CN>{make_team(), s, cnt};
-#endif
+    if constexpr (T == 1) {
+        Stack s{smem_stack + threadIdx.x, (int)blockDim.x, depth, guard, visit_limit};
+        return LaneQ<D, CN>{s, cnt};
+    } else {
+        GStack s{smem_stack + (threadIdx.x / T) * depth, depth, guard};
+        return GroupQ<D, CN>{make_team<T>(), s, cnt};
+    }
 }
 
 // host-set flag read once per team (every lane of a team must take the same
@@ -103,9 +108,9 @@ __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolvePar
                                                     int warp_uniform_points) {
     Cnt<false> cnt;
     auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
-    const Group g = make_team();
+    const Group g = make_team<1>();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = gid < total && !team_flag(g, acc.cancel);
     Walk w{};
     if (active) {
@@ -147,12 +152,12 @@ __global__ void WOST_WALK_BOUNDS k_walk_plain(const SceneView sc, const SolvePar
     }
 }
 
-template <int D, bool SCR>
+template <int D, bool SCR, int T>
 __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const SolveParams sp,
                                                          const Accumulators acc) {
     Cnt<false> cnt;
-    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
-    const Group g = make_team();
+    auto q = make_q<D, false, T>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
+    const Group g = make_team<T>();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -203,16 +208,16 @@ __global__ void WOST_WALK_BOUNDS k_walk_persistent(const SceneView sc, const Sol
 // is a sequence of such launches over a fixed grid, so no launch waits for
 // the longest walks of the solve: their steps spill into later launches
 // while the rest of the grid keeps drawing new walks.
-template <int D, bool SCR>
+template <int D, bool SCR, int T>
 __global__ void WOST_WALK_BOUNDS k_walk_resume(const SceneView sc, const SolveParams sp,
                                                      const Accumulators acc, const ResumeState rs, int iters) {
     Cnt<false> cnt;
-    auto q = make_q<D, false>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
-    const Group g = make_team();
+    auto q = make_q<D, false, T>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
+    const Group g = make_team<T>();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    float4 *slot = rs.slots + 3 * (((size_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM);
+    float4 *slot = rs.slots + 3 * (((size_t)blockIdx.x * blockDim.x + threadIdx.x) / T);
     Walk w{};
     bool have = false, drained = false;  // uniform within a team
     {
@@ -298,7 +303,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hd
     if (n_jobs <= 0) return;
     Cnt<false> cnt;
     auto q = make_q<D, false>(stack_depth, guard, cnt);
-    const Group g = make_team();
+    const Group g = make_team<1>();
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     Walk w{};
@@ -358,9 +363,9 @@ __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const So
                                                     unsigned long long *stats) {
     Cnt<true> cnt;
     auto q = make_q<D, true>(sp.stack_depth, acc.guard, cnt, sp.visit_limit);
-    const Group g = make_team();
+    const Group g = make_team<1>();
     const uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    const uint64_t gid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / WOST_TEAM;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = gid < total;
     Walk w{};
     if (active) {
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(256) k_walk_count(const SceneView sc, const So
 }
 
 // ------------------------------- launch helpers ---------------------------
-static size_t smem_bytes(int depth, int block) { return (size_t)depth * (block / WOST_TEAM) * sizeof(int2); }
+static size_t smem_bytes(int depth, int block, int lanes = 1) { return (size_t)depth * (block / lanes) * sizeof(int2); }
 
 // sets the dynamic shared-memory limit of kernel k when above the default
 static cudaError_t smem_limit(const void *k, size_t bytes) {
@@ -394,10 +399,10 @@ template <bool SCR>
 static cudaError_t walk_plain_launch(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,
                                      cudaStream_t s) {
     uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    uint64_t grid = (total * WOST_TEAM + block - 1) / block;
+    uint64_t grid = (total + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
-    int uniform = (sp.walks_per_point % (32 / WOST_TEAM) == 0) && (block % 32 == 0);
+    int uniform = (sp.walks_per_point % 32 == 0) && (block % 32 == 0);
     const void *k = sc.dim == 2 ? (const void *)k_walk_plain<2, SCR> : (const void *)k_walk_plain<3, SCR>;
     cudaError_t e = smem_limit(k, sm);
     if (e != cudaSuccess) return e;
@@ -412,7 +417,7 @@ template <bool SCR>
 static cudaError_t walk_count_launch(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                      unsigned long long *stats, int block, cudaStream_t s) {
     uint64_t total = (uint64_t)sp.n_points * (uint64_t)sp.walks_per_point;
-    uint64_t grid = (total * WOST_TEAM + block - 1) / block;
+    uint64_t grid = (total + block - 1) / block;
     if (grid > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
     size_t sm = smem_bytes(sp.stack_depth, block);
     const void *k = sc.dim == 2 ? (const void *)k_walk_count<2, SCR> : (const void *)k_walk_count<3, SCR>;
@@ -427,11 +432,11 @@ static cudaError_t walk_count_launch(const SceneView &sc, const SolveParams &sp,
 
 // resident blocks of kernel k per SM times the SM count, its shared-memory
 // limit set
-static cudaError_t resident_grid(const void *k, int block, int depth, int *blocks_out) {
+static cudaError_t resident_grid(const void *k, int block, int depth, int *blocks_out, int lanes = 1) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t sm = smem_bytes(depth, block);
+    size_t sm = smem_bytes(depth, block, lanes);
     if (e == cudaSuccess) e = smem_limit(k, sm);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, sm);
     if (e != cudaSuccess) return e;
@@ -439,31 +444,32 @@ static cudaError_t resident_grid(const void *k, int block, int depth, int *block
     return cudaSuccess;
 }
 
-template <bool SCR>
+template <bool SCR, int T>
 static cudaError_t walk_persistent_launch(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                           int block, int blocks, cudaStream_t s) {
-    size_t sm = smem_bytes(sp.stack_depth, block);
-    const void *k = sc.dim == 2 ? (const void *)k_walk_persistent<2, SCR> : (const void *)k_walk_persistent<3, SCR>;
+    size_t sm = smem_bytes(sp.stack_depth, block, T);
+    const void *k =
+        sc.dim == 2 ? (const void *)k_walk_persistent<2, SCR, T> : (const void *)k_walk_persistent<3, SCR, T>;
     cudaError_t e = smem_limit(k, sm);
     if (e != cudaSuccess) return e;
     if (sc.dim == 2)
-        k_walk_persistent<2, SCR><<<blocks, block, sm, s>>>(sc, sp, acc);
+        k_walk_persistent<2, SCR, T><<<blocks, block, sm, s>>>(sc, sp, acc);
     else
-        k_walk_persistent<3, SCR><<<blocks, block, sm, s>>>(sc, sp, acc);
+        k_walk_persistent<3, SCR, T><<<blocks, block, sm, s>>>(sc, sp, acc);
     return cudaGetLastError();
 }
 
-template <bool SCR>
+template <bool SCR, int T>
 static cudaError_t walk_resume_launch(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                       const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
-    size_t sm = smem_bytes(sp.stack_depth, block);
-    const void *k = sc.dim == 2 ? (const void *)k_walk_resume<2, SCR> : (const void *)k_walk_resume<3, SCR>;
+    size_t sm = smem_bytes(sp.stack_depth, block, T);
+    const void *k = sc.dim == 2 ? (const void *)k_walk_resume<2, SCR, T> : (const void *)k_walk_resume<3, SCR, T>;
     cudaError_t e = smem_limit(k, sm);
     if (e != cudaSuccess) return e;
     if (sc.dim == 2)
-        k_walk_resume<2, SCR><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
+        k_walk_resume<2, SCR, T><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
     else
-        k_walk_resume<3, SCR><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
+        k_walk_resume<3, SCR, T><<<blocks, block, sm, s>>>(sc, sp, acc, rs, iters);
     return cudaGetLastError();
 }
 
@@ -476,5 +482,11 @@ cudaError_t launch_walk_persistent_scr(const SceneView &sc, const SolveParams &s
                                        int block, int blocks, cudaStream_t s);
 cudaError_t launch_walk_resume_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                    const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s);
+// 8-lane team instantiations (Poisson), defined in wost_kernels_team.cu
+cudaError_t persistent_grid_team(int dim, int block, int depth, int *blocks_out);
+cudaError_t launch_walk_persistent_team(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                                        int block, int blocks, cudaStream_t s);
+cudaError_t launch_walk_resume_team(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
+                                    const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s);
 
 }  // namespace wost

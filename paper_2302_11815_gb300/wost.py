@@ -70,7 +70,7 @@ class wost_solve_desc(C.Structure):
                 ("epsilon", C.c_float), ("r_min", C.c_float), ("max_steps", C.c_int32), ("seed", C.c_uint64),
                 ("first_walk", C.c_uint32), ("kernel", C.c_int32), ("block_size", C.c_int32),
                 ("stream", C.c_void_p), ("sigma", C.c_float), ("screen_after", C.c_int32),
-                ("stack_depth", C.c_int32), ("visit_limit", C.c_int32)]
+                ("stack_depth", C.c_int32), ("visit_limit", C.c_int32), ("lanes_per_walk", C.c_int32)]
 
 
 class wost_progress(C.Structure):
@@ -264,7 +264,7 @@ def wost_scene_get_info(h) -> dict:
 
 def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
                kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
-               screen_after=0, stack_depth=0, visit_limit=0):
+               screen_after=0, stack_depth=0, visit_limit=0, lanes_per_walk=0):
     """Starts a solve.  `points` is a numpy array (host) or a torch CUDA
     tensor (device); normals/on_neumann likewise.  sigma > 0 solves the
     screened equation from step screen_after on.  stack_depth / visit_limit
@@ -272,7 +272,7 @@ def wost_solve(scene, points, walks_per_point, epsilon, r_min=0.0, max_steps=102
     lib = load()
     keep = []
     d = _solve_desc(keep, points, walks_per_point, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                    normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit)
+                    normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit, lanes_per_walk)
     h = C.c_void_p()
     _check(lib.wost_solve(scene, C.byref(d), C.byref(h)))
     return h
@@ -333,7 +333,8 @@ def wost_engine_submit(engine, scene, points, target_se, walks_cap=0, epsilon=1e
 
 class wost_tune_result(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("steps_per_second", C.c_double), ("n_tried", C.c_int32),
-                ("tried_block", C.c_int32 * 8), ("tried_steps_per_second", C.c_double * 8)]
+                ("tried_block", C.c_int32 * 8), ("tried_steps_per_second", C.c_double * 8),
+                ("lanes_per_walk", C.c_int32), ("tried_lanes", C.c_int32 * 8)]
 
 
 def wost_scene_autotune(scene, points, walks_per_point=32, epsilon=1e-3, r_min=0.0, max_steps=1024) -> dict:
@@ -342,8 +343,9 @@ def wost_scene_autotune(scene, points, walks_per_point=32, epsilon=1e-3, r_min=0
     r = wost_tune_result()
     _check(load().wost_scene_autotune(scene, _dptr(points), points.shape[0], int(walks_per_point), float(epsilon),
                                       float(r_min), int(max_steps), C.byref(r)))
-    return {"block_size": r.block_size, "steps_per_second": r.steps_per_second,
-            "tried": {int(r.tried_block[i]): float(r.tried_steps_per_second[i]) for i in range(r.n_tried)}}
+    return {"block_size": r.block_size, "lanes_per_walk": r.lanes_per_walk, "steps_per_second": r.steps_per_second,
+            "tried": {(int(r.tried_lanes[i]), int(r.tried_block[i])): float(r.tried_steps_per_second[i])
+                      for i in range(r.n_tried)}}
 
 
 def wost_engine_get_stats(engine) -> dict:
@@ -358,8 +360,9 @@ def wost_engine_destroy(engine):
 
 def _solve_desc(keep, points, walks_per_point, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0,
                 kernel="plain", block_size=0, normals=None, on_neumann=None, stream=None, sigma=0.0,
-                screen_after=0, stack_depth=0, visit_limit=0):
+                screen_after=0, stack_depth=0, visit_limit=0, lanes_per_walk=0):
     d = wost_solve_desc()
+    d.lanes_per_walk = int(lanes_per_walk)
     d.sigma = float(sigma)
     d.screen_after = int(screen_after)
     d.stack_depth = int(stack_depth)
@@ -507,10 +510,10 @@ class Scene:
 
 def solve(scene: Scene, points, walks, epsilon, r_min=0.0, max_steps=1024, seed=0, first_walk=0, kernel="plain",
           block_size=0, normals=None, on_neumann=None, stream=None, timeout=-1.0, sigma=0.0, screen_after=0,
-          stack_depth=0, visit_limit=0):
+          stack_depth=0, visit_limit=0, lanes_per_walk=0):
     """Runs a solve to completion; returns a dict of per-point statistics."""
     h = wost_solve(scene.handle, points, walks, epsilon, r_min, max_steps, seed, first_walk, kernel, block_size,
-                   normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit)
+                   normals, on_neumann, stream, sigma, screen_after, stack_depth, visit_limit, lanes_per_walk)
     try:
         wost_wait(h, timeout)
         mean, se, wd, prog = wost_poll(h, points.shape[0])

@@ -529,13 +529,47 @@ def test_autotune_picks_a_tried_block_and_keeps_the_walks(wost):
     pts = _dev(sc["points"])
     before = wost.solve(S, pts, 32, sc["epsilon"], sc["r_min"], 4096, seed=8, kernel="persistent")
     t = wost.wost_scene_autotune(S.handle, pts, 16, sc["epsilon"], sc["r_min"], 4096)
-    assert t["block_size"] in t["tried"] and len(t["tried"]) >= 2
+    assert (t["lanes_per_walk"], t["block_size"]) in t["tried"] and len(t["tried"]) == 8
+    assert {k[0] for k in t["tried"]} == {1, 8}
     assert t["steps_per_second"] == max(t["tried"].values()) > 0
-    after = wost.solve(S, pts, 32, sc["epsilon"], sc["r_min"], 4096, seed=8, kernel="persistent")
-    # the tuned launch shape runs the same walks
+    assert S.info()["lanes_per_walk"] == t["lanes_per_walk"]
+    after = wost.solve(S, pts, 32, sc["epsilon"], sc["r_min"], 4096, seed=8, kernel="persistent",
+                       lanes_per_walk=1)
+    # the tuned block size runs the same walks
     np.testing.assert_allclose(after["mean"], before["mean"], rtol=1e-9, atol=1e-12)
     assert after["total_steps"] == before["total_steps"]
     S.close()
+
+
+@pytest.mark.parametrize("kernel", ["persistent", "resumable"])
+def test_team_layout_runs_the_same_walks(wost, kernel):
+    """8 lanes per walk over the 8-wide trees (the layout the autotuner can
+    pick at run time): with h = 0 the Neumann sampler cannot change an
+    estimate, and every other query returns the same nearest answer as the
+    one-lane traversal of the binary trees, so the walks are the same (up to
+    single-precision rounding); with h != 0 against the exact solution."""
+    sc = scenes.square_scene(8, fn="linear", params=(0.0, 0.0, 1.0, 0.0), neumann_sides=("left", "right"))
+    rng = np.random.default_rng(71)
+    pts = _dev((0.05 + 0.9 * rng.random((256, 2))).astype(np.float32))
+    S = wost.Scene(sc)
+    a = wost.solve(S, pts, 64, 1e-3, 0.0, 4096, seed=3, kernel=kernel, lanes_per_walk=1)
+    b = wost.solve(S, pts, 64, 1e-3, 0.0, 4096, seed=3, kernel=kernel, lanes_per_walk=8)
+    S.close()
+    assert b["guard_flags"] == 0
+    np.testing.assert_allclose(b["mean"], a["mean"], rtol=1e-5, atol=1e-6)
+    fl = scenes.config1()
+    S = wost.Scene(fl)
+    r = wost.solve(S, _dev(fl["points"]), 512, fl["epsilon"], fl["r_min"], fl["max_steps"], seed=4, kernel=kernel,
+                   lanes_per_walk=8)
+    S.close()
+    ref = oracle.solve(oracle.Scene(fl), fl["points"], 512, fl["epsilon"], fl["r_min"], fl["max_steps"], seed=4,
+                       per_walk=True)
+    u = scenes.exact_u("exp_cos", (), fl["points"])
+    check_z(r["mean"] - u, r["se"], _allow(fl, fl["epsilon"]), label="team layout", walks=512,
+            kurt=kurtosis(ref["per_walk"]))
+    with pytest.raises(wost.WostError):  # teams serve persistent and resumable Poisson solves only
+        wost.solve(wost.Scene(fl), _dev(fl["points"]), 4, fl["epsilon"], fl["r_min"], 64, kernel="plain",
+                   lanes_per_walk=8)
 
 
 def test_cancel_and_progressive_poll(wost):
