@@ -126,6 +126,11 @@ typedef struct {
     int32_t leaf_size;         /* primitives per leaf, 0 = default (4)         */
     wost_field g_minus, h_minus; /* - side data of double-sided primitives:
                                   NONE, PER_VERTEX or PER_CORNER               */
+    int32_t silhouette_split;  /* split cost of the silhouette hierarchy:
+                                  0 = surface area x orientation (groups
+                                  candidates that face alike, Sec. 5.1.1's
+                                  suggested improvement), 1 = surface area
+                                  only (the paper's own build)                 */
 } wost_scene_desc;
 
 typedef struct {

@@ -53,11 +53,15 @@ struct BatchShared {
     DevBuf jobs[2], counters;  // counters: next walk (2D), next walk (3D), guard
     unsigned long long total[2] = {0, 0};
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    cudaStream_t own_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // the 3D launch's side stream
+    cudaStream_t own_stream = nullptr, side = nullptr;
     ~BatchShared() {
         if (ev_done) cudaEventSynchronize(ev_done);
         if (ev_start) cudaEventDestroy(ev_start);
         if (ev_done) cudaEventDestroy(ev_done);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         if (own_stream) cudaStreamDestroy(own_stream);
     }
 };

@@ -66,11 +66,56 @@ inline void empty_box(float lo[3], float hi[3]) {
     }
 }
 
-// Binned SAH over items[first, first+count); reorders items in place.
+// Normal cone of a set of silhouette candidates for the orientation-aware
+// split cost: unit axis and half angle theta in [0, pi] (pi: may face any
+// way, e.g. a boundary edge, which is always a silhouette).
+struct OCone {
+    float ax, ay, az, theta;
+};
+
+// The smallest cone holding two cones (the union used by the orientation
+// heuristic of light hierarchies, Estevez & Kulla 2018, Sec. 4.4).
+inline OCone cone_union(const OCone &a, const OCone &b) {
+    if (a.theta < 0) return b;  // empty
+    if (b.theta < 0) return a;
+    const float kPi = 3.14159265f;
+    if (a.theta >= kPi || b.theta >= kPi) return {0, 0, 1, kPi};
+    float c = std::max(-1.f, std::min(1.f, a.ax * b.ax + a.ay * b.ay + a.az * b.az));
+    float d = std::acos(c);
+    if (std::min(d + b.theta, kPi) <= a.theta) return a;
+    if (std::min(d + a.theta, kPi) <= b.theta) return b;
+    float th = 0.5f * (a.theta + d + b.theta);
+    if (th >= kPi) return {0, 0, 1, kPi};
+    // rotate a's axis toward b's by th - a.theta along their great circle
+    float r = th - a.theta, s = std::sin(d);
+    if (s < 1e-6f) return {a.ax, a.ay, a.az, th};
+    float wa = std::sin(d - r) / s, wb = std::sin(r) / s;
+    float x = wa * a.ax + wb * b.ax, y = wa * a.ay + wb * b.ay, z = wa * a.az + wb * b.az;
+    float l = std::sqrt(x * x + y * y + z * z);
+    return {x / l, y / l, z / l, th};
+}
+
+// Fraction of view directions from which a node with normal cone half angle
+// theta can hold a silhouette: those within theta of being orthogonal to the
+// cone's axis -- a band of the sphere of measure sin(theta) in 3D, 2 theta /
+// pi of the circle in 2D -- widened a little for the view cone of a node of
+// finite size.
+inline float orientation_measure(float theta, int dim) {
+    const float kHalfPi = 1.57079633f;
+    float t = std::min(theta + 0.05f, kHalfPi);
+    return dim == 3 ? std::sin(t) : t / kHalfPi;
+}
+
+// Binned SAH over items[first, first+count); reorders items in place.  With
+// per-item normal cones (the silhouette candidates) the split cost is the
+// surface-area-orientation heuristic: each side's area times its count times
+// the orientation measure of its normal cone, so that candidates facing the
+// same way are grouped and the traversal's cone test can cull them together
+// (Sec. 5.1.1 names this heuristic as the way to improve the hierarchy).
 class Builder {
   public:
-    Builder(std::vector<Item> &items, int dim, int leaf_size)
-        : it_(items), dim_(dim), leaf_(leaf_size) {}
+    Builder(std::vector<Item> &items, int dim, int leaf_size, const std::vector<OCone> *cones = nullptr)
+        : it_(items), dim_(dim), leaf_(leaf_size), cones_(cones) {}
 
     int build() {
         nodes_.reserve(2 * it_.size() + 1);
@@ -83,6 +128,8 @@ class Builder {
     static constexpr int kBins = 32;
     std::vector<Item> &it_;
     int dim_, leaf_;
+    const std::vector<OCone> *cones_;
+    float measure(const OCone &c) const { return cones_ ? orientation_measure(c.theta, dim_) : 1.f; }
 
     int make(int first, int count, int depth) {
         int id = (int)nodes_.size();
@@ -111,32 +158,41 @@ class Builder {
             if (!(ext > 0)) continue;
             float blo[kBins][3], bhi[kBins][3];
             int bcnt[kBins] = {0};
-            for (int b = 0; b < kBins; ++b) empty_box(blo[b], bhi[b]);
+            OCone bcone[kBins];
+            for (int b = 0; b < kBins; ++b) {
+                empty_box(blo[b], bhi[b]);
+                bcone[b] = {0, 0, 1, -1};
+            }
             float scale = kBins / ext;
             for (int i = first; i < first + count; ++i) {
                 int b = std::min(kBins - 1, (int)((it_[i].c[a] - clo[a]) * scale));
                 bcnt[b]++;
                 grow(blo[b], bhi[b], it_[i].lo, it_[i].hi);
+                if (cones_) bcone[b] = cone_union(bcone[b], (*cones_)[it_[i].rec]);
             }
             float rlo[3], rhi[3];
             empty_box(rlo, rhi);
             float rarea[kBins];
             int rcnt[kBins];
             int acc = 0;
+            OCone rc{0, 0, 1, -1};
             for (int b = kBins - 1; b > 0; --b) {
                 grow(rlo, rhi, blo[b], bhi[b]);
                 acc += bcnt[b];
                 rcnt[b] = acc;
-                rarea[b] = area_measure(rlo, rhi, dim_);
+                if (cones_) rc = cone_union(rc, bcone[b]);
+                rarea[b] = area_measure(rlo, rhi, dim_) * measure(rc);
             }
             float llo[3], lhi[3];
             empty_box(llo, lhi);
             int lc = 0;
+            OCone lcn{0, 0, 1, -1};
             for (int b = 0; b < kBins - 1; ++b) {
                 grow(llo, lhi, blo[b], bhi[b]);
                 lc += bcnt[b];
+                if (cones_) lcn = cone_union(lcn, bcone[b]);
                 if (lc == 0 || rcnt[b + 1] == 0) continue;
-                float cost = area_measure(llo, lhi, dim_) * lc + rarea[b + 1] * rcnt[b + 1];
+                float cost = area_measure(llo, lhi, dim_) * measure(lcn) * lc + rarea[b + 1] * rcnt[b + 1];
                 if (cost < best_cost) {
                     best_cost = cost;
                     best_axis = a;
@@ -145,6 +201,11 @@ class Builder {
             }
         }
         float parea = area_measure(nd.lo, nd.hi, dim_);
+        if (cones_) {
+            OCone pc{0, 0, 1, -1};
+            for (int i = first; i < first + count; ++i) pc = cone_union(pc, (*cones_)[it_[i].rec]);
+            parea *= measure(pc);
+        }
         // leaf if small and splitting does not pay (traversal cost 1, test cost 1)
         if (count <= leaf_ && (best_axis < 0 || 1.0f + best_cost / std::max(parea, 1e-30f) >= (float)count))
             return id;
@@ -332,7 +393,7 @@ struct WideFlattener {
 // Builds one tree over `items` (records 0..n-1) and returns the leaf order of
 // the records (perm[k] = record stored at position k).
 std::vector<int> build_tree(std::vector<Item> &items, int dim, int leaf, HostTree &t,
-                            std::vector<BNode> *keep_nodes, int *root_out) {
+                            std::vector<BNode> *keep_nodes, int *root_out, const std::vector<OCone> *cones = nullptr) {
     t.n_prims = (int)items.size();
     std::vector<int> perm(items.size());
     if (items.empty()) {
@@ -342,7 +403,7 @@ std::vector<int> build_tree(std::vector<Item> &items, int dim, int leaf, HostTre
         for (int a = 0; a < 3; ++a) t.root_lo[a] = t.root_hi[a] = 0;
         return perm;
     }
-    Builder b(items, dim, leaf);
+    Builder b(items, dim, leaf, cones);
     int root = b.build();
     for (size_t k = 0; k < items.size(); ++k) perm[k] = items[k].rec;
     Flattener fl{b.nodes_, dim, t.nodes, {}};
@@ -375,6 +436,7 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
     if (d.n_prims < 1 || !d.prims || !d.flags) return "primitives or flags missing";
     if (d.n_prims >= (int64_t)1 << 27) return "too many primitives (limit 2^27)";
     if (d.leaf_size < 0 || d.leaf_size > WOST_MAX_LEAF) return "leaf_size must be in [0, 16]";
+    if (d.silhouette_split != 0 && d.silhouette_split != 1) return "silhouette_split must be 0 or 1";
     const int leaf = d.leaf_size ? d.leaf_size : 4;
     for (int64_t i = 0; i < d.n_vertices * dim; ++i)
         if (!std::isfinite(d.vertices[i])) return "non-finite vertex coordinate";
@@ -607,9 +669,24 @@ std::string build_scene(const wost_scene_desc &d, HostScene &S) {
             it.rec = (int)i;
             items[i] = it;
         }
+        // per-candidate normal cones for the orientation-aware split cost
+        std::vector<OCone> icones(sil.size());
+        for (size_t i = 0; i < sil.size(); ++i) {
+            V3 n0 = nrm[sil[i].f0];
+            if (sil[i].f1 < 0) {
+                icones[i] = {(float)n0.x, (float)n0.y, (float)n0.z, 3.14159265f};  // always a silhouette
+                continue;
+            }
+            V3 n1 = nrm[sil[i].f1];
+            V3 s = n0 + n1;
+            double l = norm(s);
+            double half = 0.5 * std::acos(std::max(-1.0, std::min(1.0, dot(n0, n1))));
+            if (l < 1e-9) icones[i] = {(float)n0.x, (float)n0.y, (float)n0.z, 3.14159265f};
+            else icones[i] = {(float)(s.x / l), (float)(s.y / l), (float)(s.z / l), (float)half};
+        }
         std::vector<BNode> bn;
         int root = -1;
-        auto perm = build_tree(items, dim, leaf, S.S, &bn, &root);
+        auto perm = build_tree(items, dim, leaf, S.S, &bn, &root, d.silhouette_split == 1 ? nullptr : &icones);
         size_t n = sil.size();
         S.S.prims.assign(n * (dim == 2 ? 2 : 3), f4(0, 0, 0, 0));
         S.S.ids.resize(n);

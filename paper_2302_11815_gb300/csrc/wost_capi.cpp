@@ -478,14 +478,31 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
         auto t0 = std::chrono::steady_clock::now();
         CK(cudaEventRecord(shared->ev_start, stream), "cudaEventRecord");
         unsigned long long *ctr = (unsigned long long *)shared->counters.p;
+        // 2D and 3D jobs run in two kernels (each dimension its own register
+        // budget, no warp mixing both), launched CONCURRENTLY: the 3D one on a
+        // side stream forked from and joined back into the caller's, so each
+        // fills the SMs the other's tail leaves idle
+        const bool both = !jobs[0].empty() && !jobs[1].empty();
+        if (both) {
+            CK(cudaStreamCreateWithFlags(&shared->side, cudaStreamNonBlocking), "cudaStreamCreate");
+            CK(cudaEventCreateWithFlags(&shared->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+            CK(cudaEventCreateWithFlags(&shared->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+            CK(cudaEventRecord(shared->ev_fork, stream), "cudaEventRecord");
+            CK(cudaStreamWaitEvent(shared->side, shared->ev_fork, 0), "cudaStreamWaitEvent");
+        }
         for (int di = 0; di < 2; ++di) {
             if (jobs[di].empty()) continue;
             int blocks = 0;
             CK(batch_grid(di + 2, block, depth[di], &blocks), "occupancy");
             const unsigned char *base = (const unsigned char *)shared->jobs[di].p;
+            cudaStream_t ls = (both && di == 1) ? shared->side : stream;
             CK(launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)),
-                                 ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, stream),
+                                 ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, ls),
                "kernel launch");
+        }
+        if (both) {
+            CK(cudaEventRecord(shared->ev_join, shared->side), "cudaEventRecord");
+            CK(cudaStreamWaitEvent(stream, shared->ev_join, 0), "cudaStreamWaitEvent");
         }
         CK(cudaEventRecord(shared->ev_done, stream), "cudaEventRecord");
         for (int32_t i = 0; i < n; ++i) {

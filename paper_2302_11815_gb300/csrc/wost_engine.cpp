@@ -86,6 +86,8 @@ struct Round {
 struct wost_engine {
     int device = 0;
     cudaStream_t stream = nullptr, check_stream = nullptr;
+    cudaStream_t side = nullptr;                      // 3D branch of the round graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
@@ -301,11 +303,19 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
     cudaMemsetAsync(sl.counters.p, 0, 3 * 8, e->stream);
     for (int di = 0; di < 2; ++di)
         cudaMemcpyAsync(sl.jobs[di].p, sl.host[di], table_bytes(sl.cap[di]), cudaMemcpyHostToDevice, e->stream);
+    // the 2D and 3D kernels are parallel branches of the graph (the 3D one
+    // on the side stream, forked and joined inside the capture), so each
+    // fills the SMs the other's tail leaves idle
+    cudaEventRecord(e->ev_fork, e->stream);
+    cudaStreamWaitEvent(e->side, e->ev_fork, 0);
     for (int di = 0; di < 2; ++di) {
         const unsigned char *base = (const unsigned char *)sl.jobs[di].p;
         launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)), ctr + di,
-                          (unsigned int *)(ctr + 2), sl.depth[di], nullptr, e->block, blocks[di], e->stream);
+                          (unsigned int *)(ctr + 2), sl.depth[di], nullptr, e->block, blocks[di],
+                          di == 0 ? e->stream : e->side);
     }
+    cudaEventRecord(e->ev_join, e->side);
+    cudaStreamWaitEvent(e->stream, e->ev_join, 0);
     er = cudaStreamEndCapture(e->stream, &sl.graph);
     if (er != cudaSuccess) return er;
     return cudaGraphInstantiate(&sl.exec, sl.graph, 0);
@@ -493,6 +503,9 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
         }
         CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         CK(cudaStreamCreateWithFlags(&e->check_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        CK(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming), "cudaEventCreate");
         for (auto &s : e->slots) {
             CK(cudaEventCreate(&s.ev0), "cudaEventCreate");
             CK(cudaEventCreate(&s.ev1), "cudaEventCreate");
@@ -620,6 +633,9 @@ wost_status wost_engine_destroy(wost_engine *e) {
     }
     if (e->stat_host) cudaFreeHost(e->stat_host);
     cudaStreamDestroy(e->check_stream);
+    cudaEventDestroy(e->ev_fork);
+    cudaEventDestroy(e->ev_join);
+    cudaStreamDestroy(e->side);
     cudaStreamDestroy(e->stream);
     delete e;
     return WOST_OK;

@@ -48,7 +48,8 @@ class wost_scene_desc(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_vertices", C.c_int64), ("vertices", C.POINTER(C.c_float)),
                 ("n_prims", C.c_int64), ("prims", C.POINTER(C.c_int32)), ("flags", C.POINTER(C.c_uint8)),
                 ("g", wost_field), ("h", wost_field), ("f", wost_field), ("device", C.c_int32),
-                ("leaf_size", C.c_int32), ("g_minus", wost_field), ("h_minus", wost_field)]
+                ("leaf_size", C.c_int32), ("g_minus", wost_field), ("h_minus", wost_field),
+                ("silhouette_split", C.c_int32)]
 
 
 class wost_scene_info(C.Structure):
@@ -222,6 +223,7 @@ def _scene_desc(spec: dict, device: int, leaf_size: int, keep: list):
     d.h_minus = _field(spec.get("h_minus"), keep)
     d.device = device
     d.leaf_size = leaf_size
+    d.silhouette_split = int(spec.get("silhouette_split", 0))
     return d
 
 
