@@ -49,7 +49,8 @@ typedef enum {
     WOST_OK = 0,
     WOST_ERR_INVALID_ARG = 1, /* bad pointer, size, index, value or mode     */
     WOST_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed          */
-    WOST_ERR_BUDGET = 3,      /* request exceeds the engine's memory budget  */
+    WOST_ERR_BUDGET = 3,      /* the engine rejected the request (memory
+                                 budget, or its wait limit ran out)          */
     WOST_ERR_CUDA = 4,        /* a CUDA runtime call failed                  */
     WOST_ERR_TIMEOUT = 5,     /* wost_wait gave up before completion         */
     WOST_ERR_CANCELLED = 6,   /* the solve was cancelled                     */
@@ -386,7 +387,7 @@ typedef struct {
     int32_t max_walks_per_point;  /* default walk cap; 0 = 65536                           */
     int32_t block_size;           /* threads per block; 0 = 128                            */
     double max_wait_seconds;      /* a request whose first walks have not started this long
-                                     after submission is finished with TIMEOUT and counted
+                                     after submission is finished with BUDGET and counted
                                      as rejected (overload shedding); 0 = wait forever    */
 } wost_engine_desc;
 

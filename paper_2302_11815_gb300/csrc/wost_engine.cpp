@@ -341,7 +341,7 @@ bool launch_round(wost_engine *e) {
         for (Request *r : late) {
             e->st.rejected++;
             e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), r), e->pending.end());
-            finish(e, r, WOST_ERR_TIMEOUT);
+            finish(e, r, WOST_ERR_BUDGET);
         }
     }
     // active requests in admission order (the order of e->active)

@@ -35,14 +35,13 @@
 
 // Register caps of the walk kernels (2D and 3D instantiations).  They are
 // latency-bound (dependent node fetches, divergent traversals): more
-// resident warps beat the few spills a lower cap costs.  Measured on the
-// Koch workload (2D) with 128-thread blocks: uncapped (99 registers, 4
-// blocks/SM) 3.5e8 steps/s, 80 -> 3.9e8, 72 -> 4.1e8, 64 (8 blocks/SM) ->
-// 4.3e8, 56 (9 blocks/SM) -> 4.4e8, 48 -> 4.3e8; on the cube + torus
-// workload (3D): uncapped (123 registers) 5.7e7, 96 -> 6.8e7, 80 -> 7.3e7,
-// 64 -> 7.8e7.  Build-time knobs; 255 = no cap.
+// resident warps beat the few spills a lower cap costs.  Measured with the
+// warp-synchronous step and the fused Q.3/visibility traversal, 128-thread
+// blocks, steady state of the resumable kernel: Koch workload (2D) 48 ->
+// 7.8e8 steps/s, 56 -> 8.2e8, 64 -> 8.4e8, 72 -> 8.2e8; cube + torus (3D)
+// 64 -> 1.04e8, 72 -> 1.01e8, 80 -> 0.97e8.  Build-time knobs; 255 = no cap.
 #ifndef WOST_WALK_REGS_2D
-#define WOST_WALK_REGS_2D 56
+#define WOST_WALK_REGS_2D 64
 #endif
 #ifndef WOST_WALK_REGS_3D
 #define WOST_WALK_REGS_3D 64

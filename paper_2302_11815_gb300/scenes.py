@@ -739,6 +739,38 @@ def plate_cube_scene(m=3, k=4, z0=0.1, half=0.5, params=(0.5, 0.3, -0.4, 1.5)):
 
 
 # ---------------------------------------------------------------------------
+# Neumann-dominated stress scene: the "keyhole" of the paper's limitations
+# ---------------------------------------------------------------------------
+def keyhole_scene(seg=0.05, gap=0.1, window=0.4, n_points=64, seed=81):
+    """Two 2 x 2 rooms joined by a corridor 0.4 long and `gap` wide; every
+    wall is Neumann except a window of height `window` in the far wall of
+    the right room (Dirichlet).  u = x (harmonic; h = n_x on every wall).
+    Points uniform in the left room: a walk must find the corridor and then
+    the window, reflecting off Neumann walls all the way (the paper's
+    keyhole regime, Sec. 7, with mean walks of hundreds of steps)."""
+    g, w = gap / 2, window / 2
+    corners = [(-2, -1), (0, -1), (0, -g), (0.4, -g), (0.4, -1), (2.4, -1), (2.4, -w), (2.4, w), (2.4, 1),
+               (0.4, 1), (0.4, g), (0, g), (0, 1), (-2, 1)]
+    V, dirichlet = [], []
+    for k in range(len(corners)):
+        a = np.array(corners[k], float)
+        b = np.array(corners[(k + 1) % len(corners)], float)
+        n = max(1, int(np.ceil(np.linalg.norm(b - a) / seg)))
+        for i in range(n):
+            V.append(a + (b - a) * i / n)
+            dirichlet.append(k == 6)  # the window (2.4, -w) -> (2.4, w)
+    V = np.array(V)
+    P = closed_polyline(V)
+    flags = (~np.array(dirichlet)).astype(np.uint8)
+    sc = _make(2, V, P, flags, "linear", (0.0, 1.0, 0.0, 0.0), False, "analytic")
+    rng = np.random.default_rng(seed)
+    sc["points"] = np.c_[rng.uniform(-1.9, -0.1, n_points), rng.uniform(-0.9, 0.9, n_points)].astype(np.float32)
+    sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"] = 256, 1e-3, 1e-3, 1 << 20
+    sc["name"] = "keyhole_neumann_2d"
+    return sc
+
+
+# ---------------------------------------------------------------------------
 # Workload 4: many scenes of uneven size, point count and walk count
 # ---------------------------------------------------------------------------
 def radial_polygon(n, rng, base=1.0, amp=0.25, lobes=5, rough=0.03):

