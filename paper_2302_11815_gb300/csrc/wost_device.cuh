@@ -33,6 +33,12 @@
 
 #include "wost_internal.h"
 
+// Postponed-leaf traversals for Q.1, Q.2 and Q.3 + visibility (1, the
+// default) or the per-lane depth-first loops (0).  Build-time knob.
+#ifndef WOST_POSTPONE_LEAVES
+#define WOST_POSTPONE_LEAVES 1
+#endif
+
 namespace wost {
 
 // ---------------------------------------------------------------------------
@@ -699,6 +705,220 @@ __device__ __noinline__ int q_ray2(const TreeView &T, P3 o, P3 va, float tmaxA, 
 }
 
 // ---------------------------------------------------------------------------
+// Warp-wide traversals with postponed leaves (Q.1, Q.2, Q.3 + visibility)
+// ---------------------------------------------------------------------------
+// All 32 lanes of the warp call these together (act = the lane has a query).
+// A lane that reaches a leaf does not test it at once: it keeps the leaf
+// aside and goes on descending from its stack; the leaves are tested when
+// every lane either holds a leaf it cannot put aside (it already has one) or
+// has nothing left.  In the node phase all active lanes run node code and in
+// the leaf phase all run primitive code, instead of a warp paying for both
+// in almost every iteration (a node and a leaf visit of different lanes
+// serialise).  The answers are exact: pruning uses the best bound found so
+// far, which is never below the true minimum, so postponing a leaf only
+// visits some nodes a tighter bound would have pruned (the postponed
+// traversal of Aila & Laine, HPG 2009, for nearest-point and ray queries).
+template <class V>
+__device__ __forceinline__ bool spop_keep(const Stack &st, int &sp, uint32_t &ref, const V &vis) {
+    while (sp > 0) {
+        float key;
+        spop(st, sp, ref, key);
+        if (vis.keep(key)) return true;
+    }
+    return false;
+}
+
+template <int D, class V>
+__device__ __forceinline__ void spec_traverse(const TreeView &T, const Stack &st, V &vis, bool alive) {
+    constexpr unsigned FULL = 0xffffffffu;
+    uint32_t ref = T.root, pend = 0u;
+    bool have = alive, hasp = false;
+    int sp = 0;
+    unsigned visits = 0;
+    while (__any_sync(FULL, have || hasp)) {
+        for (;;) {
+            const bool step = have && !(hasp && is_leaf(ref));
+            if (!__any_sync(FULL, step)) break;
+            if (step) {
+                if (over_visit_limit(visits, T.n_nodes, st.guard, st.visit_limit)) {
+                    have = false;
+                    sp = 0;
+                } else if (is_leaf(ref)) {
+                    pend = ref;
+                    hasp = true;
+                    have = spop_keep(st, sp, ref, vis);
+                } else {
+                    vis.count_node();
+                    Node<D> n = load_node<D>(T.nodes, ref);
+                    bool h0, h1;
+                    float k0, k1;
+                    vis.children(n, ref, h0, h1, k0, k1);
+                    if (h0 && h1) {
+                        bool first0 = vis.first0(k0, k1);
+                        spush(st, sp, first0 ? n.r1 : n.r0, first0 ? k1 : k0);
+                        ref = first0 ? n.r0 : n.r1;
+                    } else if (h0 || h1) {
+                        ref = h0 ? n.r0 : n.r1;
+                    } else {
+                        have = spop_keep(st, sp, ref, vis);
+                    }
+                }
+            }
+        }
+        if (hasp) {
+            vis.leaf(leaf_first(pend), leaf_count(pend));
+            hasp = false;
+        }
+    }
+}
+
+template <int D, bool CN>
+struct ClosestVisitor {  // Q.1
+    const TreeView &T;
+    P3 x;
+    Closest best;
+    Cnt<CN> &cnt;
+    __device__ bool keep(float key) const { return key < best.d2; }
+    __device__ bool first0(float k0, float k1) const { return k0 <= k1; }
+    __device__ void count_node() { cnt.node(C_Q1); }
+    __device__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
+        k0 = box_dist2<D>(n.lo0, n.hi0, x);
+        k1 = box_dist2<D>(n.lo1, n.hi1, x);
+        h0 = k0 < best.d2;
+        h1 = k1 < best.d2;
+    }
+    __device__ void leaf(uint32_t f, uint32_t c) {
+        for (uint32_t k = f; k < f + c; ++k) {
+            cnt.prim(C_Q1);
+            Prim<D> p = load_prim<D>(T.prims, k);
+            float s0, s1;
+            P3 q = prim_closest<D>(p, x, s0, s1);
+            P3 dq = q - x;
+            float d2 = dotp<D>(dq, dq);
+            if (d2 < best.d2) {
+                best.d2 = d2;
+                best.rec = (int)k;
+                best.s0 = s0;
+                best.s1 = s1;
+                best.p = q;
+            }
+        }
+    }
+};
+
+template <int D, bool CN = false>
+__device__ Closest q_closest_w(const TreeView &T, P3 x, const Stack &st, Cnt<CN> &cnt, float bound2, bool act) {
+    ClosestVisitor<D, CN> vis{T, x, {}, cnt};
+    vis.best.d2 = bound2;
+    vis.best.rec = -1;
+    vis.best.s0 = vis.best.s1 = 0.f;
+    vis.best.p = x;
+    const bool alive = act && T.root != WOST_EMPTY_REF && box_dist2<D>(T.root_lo, T.root_hi, x) < bound2;
+    spec_traverse<D>(T, st, vis, alive);
+    return vis.best;
+}
+
+template <int D, bool CN>
+struct SilhouetteVisitor {  // Q.2
+    const TreeView &T;
+    P3 x;
+    float r2;
+    bool found;
+    Cnt<CN> &cnt;
+    __device__ bool keep(float key) const { return key < r2; }
+    __device__ bool first0(float k0, float k1) const { return k0 <= k1; }
+    __device__ void count_node() { cnt.node(C_Q2); }
+    __device__ void children(const Node<D> &n, uint32_t ref, bool &h0, bool &h1, float &k0, float &k1) const {
+        k0 = box_dist2<D>(n.lo0, n.hi0, x);
+        k1 = box_dist2<D>(n.lo1, n.hi1, x);
+        h0 = k0 < r2;
+        h1 = k1 < r2;
+        if (h0 && k0 > 0.f) h0 = has_silhouette<D>(n.lo0, n.hi0, load_cone<D>(T.cones, ref, 0), x);
+        if (h1 && k1 > 0.f) h1 = has_silhouette<D>(n.lo1, n.hi1, load_cone<D>(T.cones, ref, 1), x);
+    }
+    __device__ void leaf(uint32_t f, uint32_t c) {
+        for (uint32_t k = f; k < f + c; ++k) {
+            cnt.prim(C_Q2);
+            float d2 = sil_test<D>(T.prims, k, x, r2);
+            if (d2 < r2) {
+                r2 = d2;
+                found = true;
+            }
+        }
+    }
+};
+
+template <int D, bool CN = false>
+__device__ float q_silhouette_w(const TreeView &T, P3 x, float rmax, const Stack &st, Cnt<CN> &cnt, bool act) {
+    SilhouetteVisitor<D, CN> vis{T, x, rmax * rmax, false, cnt};
+    bool alive = act && T.root != WOST_EMPTY_REF;
+    if (alive) {
+        float d0 = box_dist2<D>(T.root_lo, T.root_hi, x);
+        alive = d0 < vis.r2 && (d0 == 0.f || has_silhouette<D>(T.root_lo, T.root_hi, T.root_cone, x));
+    }
+    spec_traverse<D>(T, st, vis, alive);
+    return vis.found ? sqrtf(vis.r2) : rmax;
+}
+
+template <int D, bool CN>
+struct Ray2Visitor {  // Q.3 (ray A) and the visibility of the Neumann sample (ray B)
+    const TreeView &T;
+    P3 o, va, vb, ia, ib;
+    float tb, tmaxB;
+    int skipB, hit;
+    bool actB, occB;
+    Cnt<CN> &cnt;
+    __device__ bool keep(float key) const { return fabsf(key) <= tb || (actB && signbit(key)); }
+    __device__ bool first0(float k0, float k1) const { return fabsf(k0) <= fabsf(k1); }
+    __device__ void count_node() { cnt.node(C_Q3); }
+    __device__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
+        float a0 = box_ray<D>(n.lo0, n.hi0, o, ia, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, ia, tb);
+        bool b0 = actB && box_ray<D>(n.lo0, n.hi0, o, ib, tmaxB) != INFINITY;
+        bool b1 = actB && box_ray<D>(n.lo1, n.hi1, o, ib, tmaxB) != INFINITY;
+        h0 = a0 != INFINITY || b0;
+        h1 = a1 != INFINITY || b1;
+        k0 = key_with_b(a0, b0);
+        k1 = key_with_b(a1, b1);
+    }
+    __device__ void leaf(uint32_t f, uint32_t c) {
+        for (uint32_t k = f; k < f + c; ++k) {
+            Prim<D> p = load_prim<D>(T.prims, k);
+            float t;
+            cnt.prim(C_Q3);
+            if (prim_ray<D>(p, o, va, tb, t, kEdgeTol)) {
+                tb = t;
+                hit = (int)k;
+            }
+            if (actB && (int)k != skipB) {
+                cnt.prim(C_VIS);
+                if (prim_ray<D>(p, o, vb, tmaxB, t, 0.f)) {
+                    occB = true;
+                    actB = false;
+                }
+            }
+        }
+    }
+};
+
+template <int D, bool CN = false>
+__device__ int q_ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t_out, bool wantB, P3 vb, int skipB,
+                        float tmaxB, bool &occB, const Stack &st, Cnt<CN> &cnt, bool act) {
+    Ray2Visitor<D, CN> vis{T, o, va, vb, mk(1.f / va.x, 1.f / va.y, D == 3 ? 1.f / va.z : 0.f),
+                           mk(1.f / vb.x, 1.f / vb.y, D == 3 ? 1.f / vb.z : 0.f), tmaxA, tmaxB, skipB, -1,
+                           act && wantB, false, cnt};
+    bool alive = act && T.root != WOST_EMPTY_REF;
+    if (alive) {
+        float a0 = box_ray<D>(T.root_lo, T.root_hi, o, vis.ia, tmaxA);
+        bool b0 = vis.actB && box_ray<D>(T.root_lo, T.root_hi, o, vis.ib, tmaxB) != INFINITY;
+        alive = a0 != INFINITY || b0;
+    }
+    spec_traverse<D>(T, st, vis, alive);
+    t_out = vis.tb;
+    occB = vis.occB;
+    return vis.hit;
+}
+
+// ---------------------------------------------------------------------------
 // Q.4 hierarchical Neumann sample (Algs. 5-6)
 // ---------------------------------------------------------------------------
 struct NSample {
@@ -924,6 +1144,38 @@ struct LaneQ {
                         float tmaxB, bool &occB) {
         return q_ray2<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt);
     }
+    // warp-wide forms: every lane of the warp calls them (act = has a query)
+#if WOST_POSTPONE_LEAVES
+    __device__ Closest closest_w(const TreeView &T, P3 x, float bound2, bool act) {
+        return q_closest_w<D, CN>(T, x, st, cnt, bound2, act);
+    }
+    __device__ float silhouette_w(const TreeView &T, P3 x, float rmax, bool act) {
+        return q_silhouette_w<D, CN>(T, x, rmax, st, cnt, act);
+    }
+    __device__ int ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
+                          float tmaxB, bool &occB, bool act) {
+        return q_ray2_w<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt, act);
+    }
+#else
+    __device__ Closest closest_w(const TreeView &T, P3 x, float bound2, bool act) {
+        Closest c;
+        c.d2 = bound2;
+        c.rec = -1;
+        c.s0 = c.s1 = 0.f;
+        c.p = x;
+        if (act) c = closest(T, x, bound2);
+        return c;
+    }
+    __device__ float silhouette_w(const TreeView &T, P3 x, float rmax, bool act) {
+        return act ? silhouette(T, x, rmax) : rmax;
+    }
+    __device__ int ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
+                          float tmaxB, bool &occB, bool act) {
+        t = tmaxA;
+        occB = false;
+        return act ? ray2(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB) : -1;
+    }
+#endif
 };
 
 // R13: inside the grown bounding box (false for a non-finite position)
@@ -971,8 +1223,9 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {  // one call site keeps the code small
         if (!__any_sync(FULL, need)) break;
+        Closest c = q.closest_w(sc.D, w.x, pass == 0 ? b * b : INFINITY, need);
         if (need) {
-            cl = q.closest(sc.D, w.x, pass == 0 ? b * b : INFINITY);
+            cl = c;
             need = cl.rec < 0;
         }
         __syncwarp();
@@ -1003,8 +1256,8 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     const float delta = sp.offset * (1.f + maxabs3(w.x));
     const P3 xq = w.onN ? w.x - w.n * delta : w.x;
     // distance to the visibility silhouette (Q.2) within d_D, star radius (R3)
-    float dsil = dD;
-    if (act) dsil = q.silhouette(sc.S, xq, dD);
+    float dsil = q.silhouette_w(sc.S, xq, dD, act);
+    if (!act) dsil = dD;
     __syncwarp();
     float r = fminf(dD, fmaxf(sp.r_min, dsil));
     // R14: at most the scene's diameter, which matters only without Dirichlet
@@ -1055,9 +1308,9 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
     // first hit with the Neumann part of the star boundary (Q.3) and the
     // visibility of z (one traversal for both rays)
     float th = r;
-    int hrec = -1;
     bool occ = false;
-    if (act) hrec = q.ray2(sc.N, xq, v, r, th, wantv, zs.z - xq, zs.rec, sp.vis_tmax, occ);
+    int hrec = q.ray2_w(sc.N, xq, v, r, th, wantv, zs.z - xq, zs.rec, sp.vis_tmax, occ, act);
+    if (!act) hrec = -1;
     __syncwarp();
     if (!act) return ended;
     P3 p, np = mk(0.f, 0.f, 0.f);

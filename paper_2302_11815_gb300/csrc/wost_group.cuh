@@ -356,6 +356,27 @@ struct GroupQ {
         return out;
     }
 
+    // warp-wide forms (every lane of the warp calls them; act is uniform
+    // within a team)
+    __device__ Closest closest_w(const TreeView &T, P3 x, float bound2, bool act) {
+        Closest c;
+        c.d2 = bound2;
+        c.rec = -1;
+        c.s0 = c.s1 = 0.f;
+        c.p = x;
+        if (act) c = closest(T, x, bound2);
+        return c;
+    }
+    __device__ float silhouette_w(const TreeView &T, P3 x, float rmax, bool act) {
+        return act ? silhouette(T, x, rmax) : rmax;
+    }
+    __device__ int ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
+                          float tmaxB, bool &occB, bool act) {
+        t = tmaxA;
+        occB = false;
+        return act ? ray2(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB) : -1;
+    }
+
     // Q.3 and the visibility test: two traversals of the wide tree
     __device__ int ray2(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
                         float tmaxB, bool &occB) {
