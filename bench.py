@@ -503,8 +503,11 @@ def sub_batch(wost, torch, args):
         return res, a.elapsed_time(b) * 1e-3
 
     rb, tb = timed(batched)
+    _log(f"batched: {tb:.1f} s")
     rp, tp = timed(lambda: per_scene("persistent"))
+    _log(f"one persistent launch per scene: {tp:.1f} s")
     rq, tq = timed(lambda: per_scene("plain"))
+    _log(f"one plain launch per scene: {tq:.1f} s")
     steps = sum(r[3]["total_steps"] for r in rb)
     walks = sum(r[3]["walks_done"] for r in rb)
     maxdiff = max(float(np.max(np.abs(a[0] - b[0]) / (np.abs(b[0]) + 1e-9))) for a, b in zip(rb, rq))
@@ -591,6 +594,7 @@ def sub_serve(wost, torch, args):
         with lock:
             live.append((h, rq, time.perf_counter()))
     window = time.perf_counter() - start
+    _log(f"serve: {offered} requests offered in {window:.1f} s, {len(done)} finished")
     drain_deadline = time.perf_counter() + args.serve_drain
     while time.perf_counter() < drain_deadline:
         with lock:
@@ -600,8 +604,10 @@ def sub_serve(wost, torch, args):
     with lock:
         for h, rq, _ in live:
             wost.wost_cancel(h)
+        _log(f"serve: drained, {len(done)} finished, {len(live)} cancelled")
     stop.set()
     th.join(timeout=120)
+    _log("serve: collector joined")
     stats = wost.wost_engine_get_stats(eng)
     wost.wost_engine_destroy(eng)
     total = time.perf_counter() - start

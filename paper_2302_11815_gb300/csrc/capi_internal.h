@@ -39,6 +39,16 @@ struct DevBuf {
         bytes = n;
         return n ? cudaMalloc(&p, n) : cudaSuccess;
     }
+    // stream-ordered allocation / release: neither waits for the device,
+    // unlike cudaMalloc / cudaFree, which synchronise with all work in flight
+    cudaError_t alloc_async(size_t n, cudaStream_t s) {
+        bytes = n;
+        return n ? cudaMallocAsync(&p, n, s) : cudaSuccess;
+    }
+    void release_async(cudaStream_t s) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
 };
 
 template <class T>
@@ -120,8 +130,13 @@ struct wost_solve_handle {
     uint64_t launches = 0;
     bool resumable() const { return kernel == WOST_KERNEL_RESUMABLE; }
     int kernel = 0;
-    int *cancel_host = nullptr;                            // mapped pinned
+    int *cancel_host = nullptr;                            // mapped pinned (engine requests: plain host)
     int *cancel_dev = nullptr;
+    // engine requests: device buffers come from the stream-ordered allocator
+    // and the cancel flag is plain host memory (the engine reads it on the
+    // host), so that destroying a request never waits for the device, whose
+    // queue the engine keeps full
+    bool engine_buffers = false;
     std::chrono::steady_clock::time_point t_launch;
     double elapsed_done = -1;
     bool done = false;
@@ -132,9 +147,15 @@ struct wost_solve_handle {
         else if (stream) cudaStreamSynchronize(stream);
         if (own_events && ev_start) cudaEventDestroy(ev_start);
         if (own_events && ev_done) cudaEventDestroy(ev_done);
+        if (engine_buffers) {
+            for (wost::DevBuf *b : {&points, &normals, &onN, &sum, &sumsq, &walks_done, &steps, &globals})
+                b->release_async(poll_stream);
+            delete cancel_host;
+        } else if (cancel_host) {
+            cudaFreeHost(cancel_host);
+        }
         if (poll_stream) cudaStreamDestroy(poll_stream);
         if (own_stream && stream) cudaStreamDestroy(stream);
-        if (cancel_host) cudaFreeHost(cancel_host);
     }
 };
 

@@ -282,20 +282,22 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     const int dim = h->dim;
     CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
     const size_t n = (size_t)d->n_points;
-    CK(h->points.alloc(n * dim * sizeof(float)), "cudaMalloc points");
+    // engine requests allocate on the engine's stream without waiting for it
+    auto alloc = [&](DevBuf &b, size_t bytes) { return h->engine_buffers ? b.alloc_async(bytes, stream) : b.alloc(bytes); };
+    CK(alloc(h->points, n * dim * sizeof(float)), "cudaMalloc points");
     cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, stream), "copy points");
     if (d->normals && d->on_neumann) {
-        CK(h->normals.alloc(n * dim * sizeof(float)), "cudaMalloc normals");
-        CK(h->onN.alloc(n), "cudaMalloc on_neumann");
+        CK(alloc(h->normals, n * dim * sizeof(float)), "cudaMalloc normals");
+        CK(alloc(h->onN, n), "cudaMalloc on_neumann");
         CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, stream), "copy normals");
         CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, stream), "copy on_neumann");
     }
-    CK(h->sum.alloc(n * 8), "cudaMalloc accumulators");
-    CK(h->sumsq.alloc(n * 8), "cudaMalloc accumulators");
-    CK(h->walks_done.alloc(n * 8), "cudaMalloc accumulators");
-    CK(h->steps.alloc(n * 8), "cudaMalloc accumulators");
-    CK(h->globals.alloc(4 * 8), "cudaMalloc accumulators");
+    CK(alloc(h->sum, n * 8), "cudaMalloc accumulators");
+    CK(alloc(h->sumsq, n * 8), "cudaMalloc accumulators");
+    CK(alloc(h->walks_done, n * 8), "cudaMalloc accumulators");
+    CK(alloc(h->steps, n * 8), "cudaMalloc accumulators");
+    CK(alloc(h->globals, 4 * 8), "cudaMalloc accumulators");
     CK(cudaMemsetAsync(h->sum.p, 0, n * 8, stream), "memset");
     CK(cudaMemsetAsync(h->sumsq.p, 0, n * 8, stream), "memset");
     CK(cudaMemsetAsync(h->walks_done.p, 0, n * 8, stream), "memset");

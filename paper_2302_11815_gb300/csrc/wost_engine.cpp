@@ -88,6 +88,7 @@ struct wost_engine {
     cudaStream_t stream = nullptr, check_stream = nullptr;
     cudaStream_t side = nullptr;                      // 3D branch of the round graph
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_admit = nullptr;                   // orders a request's poll stream after its set-up
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
@@ -145,6 +146,11 @@ void admit(wost_engine *e) {
             std::lock_guard<std::mutex> hl(r->h->mu);  // pollers see either nothing or a complete state
             s = prepare_solve(r->scene, &r->desc, e->stream, r->h);
             r->h->stream = nullptr;  // the engine's stream is not the handle's to synchronize
+            // the buffers were allocated and cleared on the engine's stream:
+            // the handle's poll stream reads them only after that
+            if (s == WOST_OK && (cudaEventRecord(e->ev_admit, e->stream) != cudaSuccess ||
+                                 cudaStreamWaitEvent(r->h->poll_stream, e->ev_admit, 0) != cudaSuccess))
+                s = fail(WOST_ERR_CUDA, "ordering the poll stream after admission");
         }
         r->pts.clear();
         r->pts.shrink_to_fit();
@@ -506,6 +512,7 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
         CK(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking), "cudaStreamCreate");
         CK(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
         CK(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_admit, cudaEventDisableTiming), "cudaEventCreate");
         for (auto &s : e->slots) {
             CK(cudaEventCreate(&s.ev0), "cudaEventCreate");
             CK(cudaEventCreate(&s.ev1), "cudaEventCreate");
@@ -575,10 +582,13 @@ wost_status wost_engine_submit(wost_engine *e, wost_scene *scene, const wost_sol
         h->dim = dim;
         h->n_points = d->n_points;
         h->walks = r->cap;
-        // the cancel flag exists before admission so that queued requests can be cancelled
-        CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
-        *h->cancel_host = 0;
-        CK(cudaHostGetDevicePointer((void **)&h->cancel_dev, h->cancel_host, 0), "cudaHostGetDevicePointer");
+        // the cancel flag exists before admission so that queued requests can
+        // be cancelled; the engine reads it on the host (it stops issuing the
+        // request's pieces), so it is plain host memory, and the request's
+        // device buffers are stream-ordered (no device-wide wait on destroy)
+        h->engine_buffers = true;
+        h->cancel_host = new int(0);
+        h->cancel_dev = nullptr;
         r->h = h.get();
         r->t_submit = Clock::now();
         {
@@ -635,6 +645,7 @@ wost_status wost_engine_destroy(wost_engine *e) {
     cudaStreamDestroy(e->check_stream);
     cudaEventDestroy(e->ev_fork);
     cudaEventDestroy(e->ev_join);
+    cudaEventDestroy(e->ev_admit);
     cudaStreamDestroy(e->side);
     cudaStreamDestroy(e->stream);
     delete e;
