@@ -368,8 +368,9 @@ wost_status wost_solve_static(wost_scene *scene, int64_t n_points, const float *
  * ranges x walk ranges) of the active requests, sized to about
  * round_seconds of GPU time but never so small that the resident grid runs
  * short of walks; the round's walk-step budget goes to the active requests
- * oldest first, so under overload the oldest complete first and the rest
- * wait (or are shed by max_wait_seconds).  Up to two rounds are queued so
+ * with the least work left in their current stage first, so under overload
+ * the cheapest complete and the rest wait (or are shed by
+ * max_wait_seconds).  Up to two rounds are queued so
  * the GPU never waits for the host.  A request runs in stages of walks per point
  * (min_walks, then growing from its own variance estimate); after each
  * stage it completes if its largest per-point standard error is at most its

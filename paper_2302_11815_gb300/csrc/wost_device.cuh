@@ -33,7 +33,7 @@
 
 #include "wost_internal.h"
 
-// Postponed-leaf traversals for Q.1, Q.2 and Q.3 + visibility (1, the
+// Postponed-leaf traversals for Q.1, Q.2 and Q.3 + visibility in 2D (1, the
 // default) or the per-lane depth-first loops (0).  Build-time knob.
 #ifndef WOST_POSTPONE_LEAVES
 #define WOST_POSTPONE_LEAVES 1
@@ -1144,38 +1144,41 @@ struct LaneQ {
                         float tmaxB, bool &occB) {
         return q_ray2<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt);
     }
-    // warp-wide forms: every lane of the warp calls them (act = has a query)
-#if WOST_POSTPONE_LEAVES
+    // warp-wide forms: every lane of the warp calls them (act = has a query).
+    // Postponed leaves in 2D only: there they gain ~9% on the Koch workload;
+    // in 3D (cube + noisy torus) they halve the rate, the silhouette query
+    // visiting far more nodes before its bound tightens.
+    static constexpr bool kPostpone = WOST_POSTPONE_LEAVES && D == 2;
     __device__ Closest closest_w(const TreeView &T, P3 x, float bound2, bool act) {
-        return q_closest_w<D, CN>(T, x, st, cnt, bound2, act);
+        if constexpr (kPostpone) {
+            return q_closest_w<D, CN>(T, x, st, cnt, bound2, act);
+        } else {
+            Closest c;
+            c.d2 = bound2;
+            c.rec = -1;
+            c.s0 = c.s1 = 0.f;
+            c.p = x;
+            if (act) c = closest(T, x, bound2);
+            return c;
+        }
     }
     __device__ float silhouette_w(const TreeView &T, P3 x, float rmax, bool act) {
-        return q_silhouette_w<D, CN>(T, x, rmax, st, cnt, act);
+        if constexpr (kPostpone) {
+            return q_silhouette_w<D, CN>(T, x, rmax, st, cnt, act);
+        } else {
+            return act ? silhouette(T, x, rmax) : rmax;
+        }
     }
     __device__ int ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
                           float tmaxB, bool &occB, bool act) {
-        return q_ray2_w<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt, act);
+        if constexpr (kPostpone) {
+            return q_ray2_w<D, CN>(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB, st, cnt, act);
+        } else {
+            t = tmaxA;
+            occB = false;
+            return act ? ray2(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB) : -1;
+        }
     }
-#else
-    __device__ Closest closest_w(const TreeView &T, P3 x, float bound2, bool act) {
-        Closest c;
-        c.d2 = bound2;
-        c.rec = -1;
-        c.s0 = c.s1 = 0.f;
-        c.p = x;
-        if (act) c = closest(T, x, bound2);
-        return c;
-    }
-    __device__ float silhouette_w(const TreeView &T, P3 x, float rmax, bool act) {
-        return act ? silhouette(T, x, rmax) : rmax;
-    }
-    __device__ int ray2_w(const TreeView &T, P3 o, P3 va, float tmaxA, float &t, bool wantB, P3 vb, int skipB,
-                          float tmaxB, bool &occB, bool act) {
-        t = tmaxA;
-        occB = false;
-        return act ? ray2(T, o, va, tmaxA, t, wantB, vb, skipB, tmaxB, occB) : -1;
-    }
-#endif
 };
 
 // R13: inside the grown bounding box (false for a non-finite position)

@@ -350,16 +350,24 @@ bool launch_round(wost_engine *e) {
             finish(e, r, WOST_ERR_BUDGET);
         }
     }
-    // active requests in admission order (the order of e->active)
+    // active requests with work left in their current stage, least
+    // remaining stage work first (admission order among equals): under
+    // overload the cheapest finish and the rest wait, instead of every
+    // request advancing slowly and none finishing
     std::vector<Request *> iss;
     for (Request *r : e->active)
         if (!r->finished && r->cursor < r->h->n_points && !cancelled(r)) iss.push_back(r);
     if (iss.empty()) return false;
+    auto left_work = [](const Request *r) {
+        return (double)(r->h->n_points - r->cursor) * (double)(r->stage_end - r->stage_begin) * r->mean_steps;
+    };
+    std::stable_sort(iss.begin(), iss.end(),
+                     [&](const Request *a, const Request *b) { return left_work(a) < left_work(b); });
     Round rd;
     rd.slot = si;
-    // the round's budget goes to the oldest requests first: each takes as
-    // many points of its current stage as the remaining budget pays for
-    // (at least one point, so every round makes progress)
+    // the round's budget goes down that order: each request takes as many
+    // points of its current stage as the remaining budget pays for (at
+    // least one point, so every round makes progress)
     double remaining = std::max(e->round_budget_steps, e->min_round_steps);
     for (Request *r : iss) {
         if (remaining <= 0) break;
