@@ -412,7 +412,8 @@ def sub_cube_torus(wost, torch, args, stream, flush, peaks, peak_src, l2_gbs, hb
     sub = pts[rng.choice(len(pts), 4096, replace=False)]
     r = wost.solve(S, torch.from_numpy(sub[:512]).cuda(), 32, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=3,
                    kernel="counting")
-    b_step, f_step = work_per_step(r["counts"], r["total_steps"], 3, info)
+    b_step, f_step = work_per_step(r["counts"], r["total_steps"], 3, dict(info, lanes_per_walk=1, node_bytes=64,
+                                                                         cone_bytes=32))
     pts_dev = torch.from_numpy(pts).cuda()
     job, steps, secs, ms = _resumable_launches(wost, torch, S, pts_dev, sc, stream, flush, args.iters3, 2,
                                                args.steps3, seed=31)
@@ -533,6 +534,23 @@ def sub_batch(wost, torch, args):
             "note": "same walks in all three forms (keyed random streams), so equal RMS error by construction"}
 
 
+_SERVE_SCENES = {}
+
+
+def sub_serve_knee(wost, torch, args):
+    """The serving workload at a rate the GPU keeps up with (near the knee
+    of served against offered load) and with a smaller per-request walk
+    cap, so that completed requests give latency percentiles."""
+    import copy
+
+    a = copy.copy(args)
+    a.serve_rate, a.serve_seconds = args.knee_rate, args.knee_seconds
+    a.serve_walk_cap, a.serve_drain = args.knee_walk_cap, args.knee_drain
+    out = sub_serve(wost, torch, a)
+    out["workload"] = "serve_8_scenes_3d_knee"
+    return out
+
+
 def sub_serve(wost, torch, args):
     """Workload 5: 8 resident 3D scenes (cube + noisy torus, ~5M triangles
     together), a Poisson stream of requests into the serving engine
@@ -543,12 +561,15 @@ def sub_serve(wost, torch, args):
     from paper_2302_11815_gb300 import scenes
 
     t0 = time.perf_counter()
-    specs = scenes.config5_scenes(total=args.serve_total_prims)
-    S = [wost.Scene(s) for s in specs]
+    key = (args.serve_total_prims, args.serve_max_points)
+    if key not in _SERVE_SCENES:  # resident scenes and point pools, shared by both serving runs
+        specs = scenes.config5_scenes(total=args.serve_total_prims)
+        rng = np.random.default_rng(7)
+        _SERVE_SCENES[key] = (specs, [wost.Scene(s) for s in specs],
+                              [scenes.plane_points(rng, int(args.serve_max_points), s["tube"]) for s in specs])
+    specs, S, pools = _SERVE_SCENES[key]
     reqs = scenes.config5_requests(duration_s=args.serve_seconds, rate=args.serve_rate,
                                    points=(1e3, args.serve_max_points))
-    rng = np.random.default_rng(7)
-    pools = [scenes.plane_points(rng, int(args.serve_max_points), s["tube"]) for s in specs]
     setup_s = time.perf_counter() - t0
     eng = wost.wost_engine_create(round_seconds=args.round_seconds, max_walks_per_point=args.serve_walk_cap,
                                   max_wait_seconds=args.serve_max_wait)
@@ -613,8 +634,6 @@ def sub_serve(wost, torch, args):
     total = time.perf_counter() - start
     ok = [d for d in done if d["status"] == "ok"]
     lat = np.array([d["latency"] for d in ok]) if ok else np.array([np.nan])
-    for s in S:
-        s.close()
     return {"workload": "serve_8_scenes_3d", "metric": "p99_latency_s",
             "p50_latency_s": float(np.nanpercentile(lat, 50)) if ok else None,
             "p99_latency_s": float(np.nanpercentile(lat, 99)) if ok else None,
@@ -646,8 +665,15 @@ def run_ours(args):
     grid_pts = np.ascontiguousarray(sc["points"], np.float32)
     walks = sc["walks"]
     S = wost.Scene(sc, device=local)
+    _log(f"scene built: {S.info()['n_dirichlet']} D + {S.info()['n_neumann']} N prims, {len(grid_pts)} grid points")
+    tune = None
+    if not args.block:
+        # the library's autotuner picks the layout (lanes per walk) and block
+        # size on a sample of the grid; the timed launches use its choice
+        sample = torch.from_numpy(grid_pts[:: max(1, len(grid_pts) // 8192)].copy()).cuda()
+        tune = wost.wost_scene_autotune(S.handle, sample, 8, sc["epsilon"], sc["r_min"], sc["max_steps"])
+        _log(f"autotune: {tune['lanes_per_walk']} lane(s) per walk, block {tune['block_size']}")
     info = S.info()
-    _log(f"scene built: {info['n_dirichlet']} D + {info['n_neumann']} N prims, {len(grid_pts)} grid points")
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     seed0 = 1000 * (rank + 1)
@@ -656,7 +682,10 @@ def run_ours(args):
     sub = torch.from_numpy(grid_pts[:: args.count_stride * 64].copy()).cuda()
     r = wost.solve(S, sub, walks, sc["epsilon"], sc["r_min"], sc["max_steps"], seed=seed0, kernel="counting",
                    timeout=600.0)
-    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2, info)
+    # the counting kernel traverses the binary trees one lane per walk: its
+    # visit counts go with that layout's record sizes
+    model_info = dict(info, lanes_per_walk=1, node_bytes=48, cone_bytes=32)
+    bytes_step, flops_step = work_per_step(r["counts"], r["total_steps"], 2, model_info)
     _log(f"work model: {r['total_steps']} steps counted, {bytes_step:.0f} B and {flops_step:.0f} flop per step")
 
     # The job: every grid point x 256 walks (36 million walks, ~1.1e11 walk
@@ -731,7 +760,8 @@ def run_ours(args):
                                                                   l2_gbs, hbm_gbs, fp32, fp32_src)),
                          ("keyhole", lambda: sub_keyhole(wost, torch, stream)),
                          ("batch", lambda: sub_batch(wost, torch, args)),
-                         ("serve", lambda: sub_serve(wost, torch, args))):
+                         ("serve", lambda: sub_serve(wost, torch, args)),
+                         ("serve_knee", lambda: sub_serve_knee(wost, torch, args))):
             _log(f"workload {name}")
             try:
                 line_extra[name] = fn()
@@ -745,7 +775,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config_block(sc, {"kernel": "resumable", "block": args.block or 128,
+            "autotune": None if tune is None else {
+                "chosen": {"lanes_per_walk": tune["lanes_per_walk"], "block": tune["block_size"]},
+                "tried_steps_per_s": {f"{k[0]}x{k[1]}": v for k, v in tune["tried"].items()}},
+            "config": _config_block(sc, {"kernel": "resumable",
+                                         "block": args.block or (tune["block_size"] if tune else 128),
+                                         "lanes_per_walk": info["lanes_per_walk"],
                                          "parallelism": f"replicas x{world}",
                                          "step": f"one launch of the whole-grid job ({n_all} points x {walks} walks):"
                                                  f" every resident lane runs up to {args.iters} walk steps, drawing"
@@ -847,6 +882,10 @@ def main():
     ap.add_argument("--serve-walk-cap", type=int, default=4096)
     ap.add_argument("--serve-max-wait", type=float, default=5.0)
     ap.add_argument("--serve-drain", type=float, default=30.0)
+    ap.add_argument("--knee-rate", type=float, default=0.5, help="requests/s of the second serving run")
+    ap.add_argument("--knee-seconds", type=float, default=40.0)
+    ap.add_argument("--knee-walk-cap", type=int, default=256)
+    ap.add_argument("--knee-drain", type=float, default=30.0)
     ap.add_argument("--iters3", type=int, default=1024, help="walk steps per lane per launch, 3D workload")
     ap.add_argument("--steps3", type=int, default=5, help="timed launches, 3D workload")
     ap.add_argument("--headline-only", action="store_true", help="skip the other workloads")

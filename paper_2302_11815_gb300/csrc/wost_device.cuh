@@ -77,6 +77,25 @@ static __device__ __noinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     }
     return c;
 }
+// One out-of-line copy of each library function the walk step needs.  Inlined
+// at every call site, their range reductions and slow paths were a fifth of
+// the walk kernels' code, and instruction supply is what stalls those
+// kernels most (ncu: no_instruction the leading stall reason).
+static __device__ __noinline__ float m_exp(float a) { return expf(a); }
+static __device__ __noinline__ float m_log(float a) { return logf(a); }
+static __device__ __noinline__ float m_asin(float a) { return asinf(a); }
+static __device__ __noinline__ void m_sincos(float a, float *s, float *c) { sincosf(a, s, c); }
+__device__ __forceinline__ float m_sin(float a) {
+    float s, c;
+    m_sincos(a, &s, &c);
+    return s;
+}
+__device__ __forceinline__ float m_cos(float a) {
+    float s, c;
+    m_sincos(a, &s, &c);
+    return c;
+}
+
 // (0,1): top 23 bits plus one half, times 2^-23 (exact in FP32)
 __device__ __forceinline__ float u01(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
 
@@ -91,7 +110,7 @@ struct Stream {  // sequential uniforms from slots 1, 2, ... of one (walk, point
         k1 = key1;
         used = 4;
     }
-    __device__ __forceinline__ float next() {
+    __device__ __noinline__ float next() {  // one copy: ~14 draws per step from 4 call sites
         if (used == 4) {
             buf = philox10(ctr, k0, k1);
             ctr.w += 1u;
@@ -254,7 +273,7 @@ __device__ __forceinline__ Prim<D> load_prim(const float4 *prims, uint32_t k) {
 __device__ __forceinline__ float seg_param(P3 a, P3 b, P3 x, int dimz) {
     P3 e = b - a, ap = x - a;
     float ee = e.x * e.x + e.y * e.y + (dimz ? e.z * e.z : 0.f);
-    float t = (ap.x * e.x + ap.y * e.y + (dimz ? ap.z * e.z : 0.f)) / ee;
+    float t = __fdividef(ap.x * e.x + ap.y * e.y + (dimz ? ap.z * e.z : 0.f), ee);
     return fminf(fmaxf(t, 0.f), 1.f);
 }
 
@@ -270,7 +289,7 @@ __device__ __forceinline__ P3 tri_closest(P3 a, P3 b, P3 c, P3 p, float &v, floa
     if (d3 >= 0.f && d4 <= d3) { v = 1.f; w = 0.f; return b; }
     float vc = d1 * d4 - d3 * d2;
     if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
-        float t = d1 / (d1 - d3);
+        float t = __fdividef(d1, d1 - d3);
         v = t; w = 0.f;
         return a + ab * t;
     }
@@ -279,17 +298,17 @@ __device__ __forceinline__ P3 tri_closest(P3 a, P3 b, P3 c, P3 p, float &v, floa
     if (d6 >= 0.f && d5 <= d6) { v = 0.f; w = 1.f; return c; }
     float vb = d5 * d2 - d1 * d6;
     if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
-        float t = d2 / (d2 - d6);
+        float t = __fdividef(d2, d2 - d6);
         v = 0.f; w = t;
         return a + ac * t;
     }
     float va = d3 * d6 - d5 * d4;
     if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
-        float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        float t = __fdividef(d4 - d3, (d4 - d3) + (d5 - d6));
         v = 1.f - t; w = t;
         return b + (c - b) * t;
     }
-    float den = 1.f / (va + vb + vc);
+    float den = __fdividef(1.f, va + vb + vc);
     v = vb * den;
     w = vc * den;
     return a + ab * v + ac * w;
@@ -345,7 +364,7 @@ __device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tma
         P3 e = p.b - p.a, ao = p.a - o;
         float den = v.x * e.y - v.y * e.x;
         if (den == 0.f) return false;
-        float inv = 1.f / den;
+        float inv = __fdividef(1.f, den);
         float tt = (ao.x * e.y - ao.y * e.x) * inv;
         float u = (ao.x * v.y - ao.y * v.x) * inv;
         if (u < -tol || u > 1.f + tol || !(tt > 0.f) || tt > tmax) return false;
@@ -356,7 +375,7 @@ __device__ __forceinline__ bool prim_ray(const Prim<D> &p, P3 o, P3 v, float tma
         P3 pv = crossp(v, e2);
         float det = dotp<3>(e1, pv);
         if (det == 0.f) return false;
-        float inv = 1.f / det;
+        float inv = __fdividef(1.f, det);
         P3 tv = o - p.a;
         float u = dotp<3>(tv, pv) * inv;
         if (u < -tol || u > 1.f + tol) return false;
@@ -960,7 +979,7 @@ __device__ NSample q_sample(const TreeView &T, P3 x, float r, Stream &rng, Cnt<C
         }
         float tot = w0 + w1;
         if (!(tot > 0.f)) return out;
-        float p0 = w0 / tot;
+        float p0 = __fdividef(w0, tot);  // the decision and the pdf use this same p0
         if (rng.next() < p0) {
             pdf *= p0;
             ref = n.r0;
@@ -1018,17 +1037,17 @@ __device__ NSample q_sample(const TreeView &T, P3 x, float r, Stream &rng, Cnt<C
 template <int D>
 __device__ __noinline__ float fn_u(int fn, const float *p, P3 x) {
     switch (fn) {
-    case 1: return expf(x.x) * cosf(x.y);
-    case 2: return sinf(2.f * x.x) * cosf(3.f * x.y);
+    case 1: return m_exp(x.x) * m_cos(x.y);
+    case 2: return m_sin(2.f * x.x) * m_cos(3.f * x.y);
     case 3: return x.x * x.x - x.y * x.y + 0.5f * x.z;
     case 4: return (1.f - (x.x * x.x + x.y * x.y + x.z * x.z)) / (2.f * D);
     case 5: return p[0] + p[1] * x.x + p[2] * x.y + p[3] * x.z;
     case 6: {
         P3 d = x - mk(p[2], p[3], D == 3 ? p[4] : 0.f);
         float rho = sqrtf(dotp<D>(d, d));
-        return D == 2 ? p[0] + p[1] * logf(rho) : p[0] + p[1] / rho;
+        return D == 2 ? p[0] + p[1] * m_log(rho) : p[0] + p[1] / rho;
     }
-    case 7: return p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
+    case 7: return p[0] * m_exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     default: return 0.f;
     }
 }
@@ -1036,10 +1055,16 @@ template <int D>
 __device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
     switch (fn) {
     case 1: {
-        float e = expf(x.x);
-        return mk(e * cosf(x.y), -e * sinf(x.y), 0.f);
+        float e = m_exp(x.x), s, c;
+        m_sincos(x.y, &s, &c);
+        return mk(e * c, -e * s, 0.f);
     }
-    case 2: return mk(2.f * cosf(2.f * x.x) * cosf(3.f * x.y), -3.f * sinf(2.f * x.x) * sinf(3.f * x.y), 0.f);
+    case 2: {
+        float s2, c2, s3, c3;
+        m_sincos(2.f * x.x, &s2, &c2);
+        m_sincos(3.f * x.y, &s3, &c3);
+        return mk(2.f * c2 * c3, -3.f * s2 * s3, 0.f);
+    }
     case 3: return mk(2.f * x.x, -2.f * x.y, 0.5f);
     case 4: return x * (-1.f / D);
     case 5: return mk(p[1], p[2], p[3]);
@@ -1049,7 +1074,7 @@ __device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
         return D == 2 ? d * (p[1] / rho2) : d * (-p[1] / (rho2 * sqrtf(rho2)));
     }
     case 7: {
-        float u = p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
+        float u = p[0] * m_exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
         return mk(u * p[1], u * p[2], u * p[3]);
     }
     default: return mk(0.f, 0.f, 0.f);
@@ -1057,9 +1082,9 @@ __device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
 }
 template <int D>
 __device__ __noinline__ float fn_neglap(int fn, const float *p, P3 x) {
-    if (fn == 2) return 13.f * sinf(2.f * x.x) * cosf(3.f * x.y);
+    if (fn == 2) return 13.f * m_sin(2.f * x.x) * m_cos(3.f * x.y);
     if (fn == 4) return 1.f;
-    if (fn == 7) return -(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]) * p[0] * expf(p[1] * x.x + p[2] * x.y + p[3] * x.z);
+    if (fn == 7) return -(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]) * p[0] * m_exp(p[1] * x.x + p[2] * x.y + p[3] * x.z);
     return 0.f;
 }
 
@@ -1339,7 +1364,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
         } else {
             hv = corner_interp<D>(minus ? sc.N.data_minus : sc.N.data, zs.rec, zs.s0, zs.s1);
         }
-        float G = D == 2 ? logf(r / dzl) * (0.5f / 3.14159265358979f)
+        float G = D == 2 ? m_log(__fdividef(r, dzl)) * (0.5f / 3.14159265358979f)
                          : (1.f / dzl - 1.f / r) * (0.25f / 3.14159265358979f);
         if constexpr (SCR) {
             if (sqs > 0.f) G = screened_green<D>(dzl, r, sqs);
@@ -1354,7 +1379,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
         if constexpr (D == 2) {
             ts = r * sqrtf(u01(rb.y) * u01(rb.z));
         } else {
-            ts = r * (0.5f + sinf(asinf(2.f * u01(rb.z) - 1.f) * (1.f / 3.f)));
+            ts = r * (0.5f + m_sin(m_asin(2.f * u01(rb.z) - 1.f) * (1.f / 3.f)));
         }
         P3 pd = p - w.x;
         if (ts * ts < dotp<D>(pd, pd)) {
@@ -1363,7 +1388,7 @@ __device__ bool walk_step(const SceneView &sc, const SolveParams &sp, Walk &w, Q
             float wS = (D == 2 ? 0.25f : (1.f / 6.f)) * r * r;
             if constexpr (SCR) {
                 if (sqs > 0.f) {  // R15: the unscreened sample reweighted by G^sigma_B / G_B
-                    float G0 = D == 2 ? logf(r / ts) * (0.5f / 3.14159265358979f)
+                    float G0 = D == 2 ? m_log(__fdividef(r, ts)) * (0.5f / 3.14159265358979f)
                                       : (1.f / ts - 1.f / r) * (0.25f / 3.14159265358979f);
                     wS *= screened_green<D>(ts, r, sqs) / G0;
                 }
