@@ -645,6 +645,7 @@ def sub_serve(wost, torch, args):
             "reached_walk_cap": int(stats["capped"]),
             "served_points_per_s": sum(d["n"] for d in ok) / total,
             "served_walk_steps_per_s": sum(d["steps"] for d in ok) / total,
+            "engine_walk_steps_per_s": stats["walk_steps"] / total,
             "engine": stats, "window_s": window, "total_s": total, "setup_s": setup_s,
             "scene_prims": [int(len(s["prims"])) for s in specs],
             "config": {"rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
@@ -854,16 +855,19 @@ def run_profile_case(args):
     pts = torch.from_numpy(np.ascontiguousarray(sc["points"], np.float32)).cuda()
     h = wost.wost_solve(S.handle, pts, sc["walks"], sc["epsilon"], sc["r_min"], sc["max_steps"], seed=5,
                         kernel="resumable", block_size=args.block)
-    out = []
+    out, steps, before = [], [], 0
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         wost.wost_solve_advance(h, args.iters)
         torch.cuda.synchronize()
         out.append(time.perf_counter() - t0)
-    _, _, _, pr = wost.wost_poll(h, len(pts))
+        _, _, _, pr = wost.wost_poll(h, len(pts))
+        steps.append(int(pr["steps_run"]) - before)  # walk steps of this launch (divides ncu's bytes)
+        before = int(pr["steps_run"])
     wost.wost_solve_destroy(h)
     print(json.dumps({"mode": "profile", "points": len(pts), "launches": int(pr["launches"]),
-                      "iters": args.iters, "steps_run": int(pr["steps_run"]), "launch_s": out}), flush=True)
+                      "iters": args.iters, "steps_run": before, "steps_per_launch": steps, "launch_s": out}),
+          flush=True)
     S.close()
     return 0
 
@@ -883,8 +887,8 @@ def main():
     ap.add_argument("--serve-max-wait", type=float, default=5.0)
     ap.add_argument("--serve-drain", type=float, default=30.0)
     ap.add_argument("--knee-rate", type=float, default=0.5, help="requests/s of the second serving run")
-    ap.add_argument("--knee-seconds", type=float, default=40.0)
-    ap.add_argument("--knee-walk-cap", type=int, default=256)
+    ap.add_argument("--knee-seconds", type=float, default=60.0)
+    ap.add_argument("--knee-walk-cap", type=int, default=64)
     ap.add_argument("--knee-drain", type=float, default=30.0)
     ap.add_argument("--iters3", type=int, default=1024, help="walk steps per lane per launch, 3D workload")
     ap.add_argument("--steps3", type=int, default=5, help="timed launches, 3D workload")

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define WOST_ABI_VERSION 3
+#define WOST_ABI_VERSION 4
 
 typedef enum {
     WOST_OK = 0,
@@ -397,9 +397,13 @@ typedef struct {
     int32_t queued, active;
     uint64_t rounds;
     uint64_t graph_launches;      /* rounds launched by replaying a CUDA graph   */
-    double gpu_seconds;           /* summed GPU time of finished rounds          */
+    double gpu_seconds;           /* summed duration of finished rounds (rounds
+                                     overlap on the device: may exceed wall time) */
     int64_t budget_bytes, used_bytes;
     double round_budget_steps;    /* current walk-step budget of one round       */
+    uint64_t walk_steps;          /* walk steps of every walk finished by a
+                                     finished round (completed, cancelled and
+                                     shed requests alike)                        */
 } wost_engine_stats;
 
 wost_status wost_engine_create(const wost_engine_desc *desc, wost_engine **out);
@@ -464,10 +468,13 @@ typedef struct {
     int32_t tried_lanes[8];
 } wost_tune_result;
 
-/* Times the persistent kernel on a sample of the caller's points (device
- * pointer, n points, at most 8192 used) for each layout -- one lane per walk
- * over the binary trees, 8-lane teams over the 8-wide trees -- and block
- * sizes 64..256 (8 combinations), and keeps the fastest block size as the
+/* Times the walk loop in steady state -- the resumable kernel, one launch
+ * of 256 steps per lane to fill the lanes, then two timed launches (walk
+ * steps executed over device time) -- on an evenly strided sample of the
+ * caller's points (device pointer, n points, at most 65,536 used) at
+ * walks_per_point (0: 32), for each layout -- one lane per walk over the
+ * binary trees, 8-lane teams over the 8-wide trees -- and block sizes
+ * 64..256 (8 combinations), and keeps the fastest block size as the
  * scene's default for persistent, batched and engine launches whose
  * block_size is 0, and the fastest layout as its default for persistent and
  * resumable Poisson solves whose lanes_per_walk is 0 (wost_scene_info then

@@ -802,35 +802,59 @@ wost_status wost_scene_autotune(wost_scene *scene, const float *points, int64_t 
     try {
         if (!scene || !points || !out || n < 1) return fail(WOST_ERR_INVALID_ARG, "null argument or n < 1");
         std::memset(out, 0, sizeof *out);
-        const int64_t m = std::min<int64_t>(n, 8192);
+        CK(cudaSetDevice(scene->device), "cudaSetDevice");
+        // an evenly strided sample of the caller's points (a prefix could
+        // hold one region of the domain only)
+        const int dim = scene->view.dim;
+        const int64_t m = std::min<int64_t>(n, 65536), stride = n / m;
+        DevBuf sample;
+        CK(sample.alloc((size_t)m * dim * sizeof(float)), "cudaMalloc");
+        CK(cudaMemcpy2D(sample.p, dim * sizeof(float), points, (size_t)stride * dim * sizeof(float),
+                        dim * sizeof(float), (size_t)m, cudaMemcpyDeviceToDevice),
+           "sample copy");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(cudaEventCreate(&e0), "cudaEventCreate");
+        CK(cudaEventCreate(&e1), "cudaEventCreate");
+        std::unique_ptr<CUevent_st, cudaError_t (*)(cudaEvent_t)> k0(e0, cudaEventDestroy), k1(e1, cudaEventDestroy);
         const int blocks[4] = {64, 128, 192, 256};
+        const int iters = 256;  // walk steps per lane per launch
         double best = -1;
         for (int ci = 0; ci < 8; ++ci) {
             const int bi = ci % 4, lanes = ci < 4 ? 1 : WOST_WIDE;
             wost_solve_desc d{};
             d.lanes_per_walk = lanes;
             d.n_points = m;
-            d.points = points;
+            d.points = (const float *)sample.p;
             d.memory = WOST_MEM_DEVICE;
             d.walks_per_point = walks > 0 ? walks : 32;
             d.epsilon = epsilon;
             d.r_min = r_min;
             d.max_steps = max_steps;
-            d.seed = 0x5EED0000u + (uint64_t)bi;
-            d.kernel = WOST_KERNEL_PERSISTENT;
+            d.seed = 0x5EED0000u;
+            d.kernel = WOST_KERNEL_RESUMABLE;
             d.block_size = blocks[bi];
-            double rate = 0;
-            for (int rep = 0; rep < 2; ++rep) {  // the first run warms caches and the module
-                wost_solve_handle *h = nullptr;
-                wost_status st = wost_solve(scene, &d, &h);
-                if (st != WOST_OK) return st;
-                st = wost_wait(h, -1);
-                wost_progress pr{};
-                if (st == WOST_OK) st = wost_poll(h, nullptr, nullptr, nullptr, &pr);
-                wost_solve_destroy(h);
-                if (st != WOST_OK) return st;
-                rate = pr.elapsed_seconds > 0 ? (double)pr.total_steps / pr.elapsed_seconds : 0;
-            }
+            // steady state of the resumable kernel: one launch fills every
+            // lane with a walk, the next two are timed (walk steps executed
+            // over their device time); a sample too small to keep the lanes
+            // busy is timed as it drains, which is then its real regime
+            wost_solve_handle *h = nullptr;
+            wost_status st = wost_solve(scene, &d, &h);
+            if (st != WOST_OK) return st;
+            std::unique_ptr<wost_solve_handle, wost_status (*)(wost_solve_handle *)> hk(h, wost_solve_destroy);
+            const cudaStream_t s = h->stream;
+            unsigned long long before = 0, after = 0;
+            if ((st = wost_solve_advance(h, iters, nullptr)) != WOST_OK) return st;
+            CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            CK(cudaMemcpy(&before, h->rstate.p, sizeof before, cudaMemcpyDeviceToHost), "copy steps");
+            CK(cudaEventRecord(e0, s), "cudaEventRecord");
+            for (int rep = 0; rep < 2; ++rep)
+                if ((st = wost_solve_advance(h, iters, nullptr)) != WOST_OK) return st;
+            CK(cudaEventRecord(e1, s), "cudaEventRecord");
+            CK(cudaEventSynchronize(e1), "cudaEventSynchronize");
+            CK(cudaMemcpy(&after, h->rstate.p, sizeof after, cudaMemcpyDeviceToHost), "copy steps");
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+            const double rate = ms > 0 ? (double)(after - before) / (ms * 1e-3) : 0;
             out->tried_block[out->n_tried] = blocks[bi];
             out->tried_lanes[out->n_tried] = lanes;
             out->tried_steps_per_second[out->n_tried] = rate;

@@ -5,11 +5,14 @@
 // persistent launch (k_walk_batch, one per dimension present) over "pieces"
 // -- point ranges x walk ranges -- of every active request, sized so that a
 // round takes about round_seconds of GPU time (the walk-step budget adapts to
-// the measured round times).  Two rounds may be queued on the stream, so the
-// host prepares round k+1 while the GPU runs round k and the GPU never idles
-// between rounds.  Requests are admitted FIFO by device-memory budget, run in
-// stages of walks per point, and are checked after each stage with the
-// per-solve summary kernel (k_request_stats) on a second stream.
+// the measured round times).  Every round slot has streams of its own and up
+// to three rounds are in flight: a round lasts until its longest walk ends,
+// and the next rounds' blocks take the SMs that its finished blocks free, so
+// the tail of one round overlaps the bulk of the next and the host prepares
+// rounds while the GPU runs earlier ones.  Requests are admitted FIFO by
+// device-memory budget, run in stages of walks per point, and are checked
+// after each stage with the per-solve summary kernel (k_request_stats) on a
+// high-priority stream (its blocks go first when SMs free up).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -53,17 +56,21 @@ struct Piece {
 // One scheduling slot: device job tables (BatchHeader + jobs, per
 // dimension), their pinned staging copies, and the CUDA graph of one round:
 // reset counters, upload both tables, launch the 2D and the 3D batched
-// kernels (a kernel whose table is empty returns at once).  A round replays
-// the graph; it is re-captured only when a table outgrows its capacity or a
-// deeper scene needs a larger traversal stack.
+// kernels as parallel branches (a kernel whose table is empty returns at
+// once), copy the round's walk-step count to the host.  A round replays the
+// graph on the slot's own stream; it is re-captured only when a table
+// outgrows its capacity or a deeper scene needs a larger traversal stack.
 struct Slot {
     DevBuf jobs[2];
     unsigned char *host[2] = {nullptr, nullptr};
     size_t cap[2] = {0, 0};    // jobs per table
     int depth[2] = {0, 0};     // stack entries the graph was captured with
-    DevBuf counters;           // next walk 2D, next walk 3D, guard
+    DevBuf counters;           // next walk 2D, next walk 3D, guard, walk steps run
+    unsigned long long *steps_host = nullptr;  // pinned copy of the walk-step count
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr;  // the round; its 3D branch
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool busy = false;
     ~Slot() {
@@ -71,8 +78,15 @@ struct Slot {
         if (graph) cudaGraphDestroy(graph);
         for (auto *h : host)
             if (h) cudaFreeHost(h);
+        if (steps_host) cudaFreeHost(steps_host);
+        for (cudaEvent_t ev : {fork, join, ev0, ev1})
+            if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t st : {stream, side})
+            if (st) cudaStreamDestroy(st);
     }
 };
+
+constexpr int kSlots = 3;  // rounds in flight at most
 
 size_t table_bytes(size_t jobs) { return sizeof(BatchHeader) + jobs * sizeof(BatchJob); }
 
@@ -85,10 +99,9 @@ struct Round {
 
 struct wost_engine {
     int device = 0;
-    cudaStream_t stream = nullptr, check_stream = nullptr;
-    cudaStream_t side = nullptr;                      // 3D branch of the round graph
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream = nullptr, check_stream = nullptr;  // admissions; stage checks
     cudaEvent_t ev_admit = nullptr;                   // orders a request's poll stream after its set-up
+    cudaEvent_t ev_ready = nullptr;                   // orders a round after the admissions before it
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
@@ -100,7 +113,7 @@ struct wost_engine {
     std::vector<Request *> active;
     std::unordered_map<wost_solve_handle *, Request *> by_handle;
     std::deque<Round> inflight;
-    Slot slots[3];
+    Slot slots[kSlots];
     double round_budget_steps = 4e6;
     wost_engine_stats st{};
     bool stop = false;
@@ -237,15 +250,16 @@ void check_stages(wost_engine *e, std::vector<Request *> &ready) {
     }
 }
 
-void retire_front(wost_engine *e) {
-    Round rd = std::move(e->inflight.front());
-    e->inflight.pop_front();
+void retire(wost_engine *e, size_t i) {
+    Round rd = std::move(e->inflight[i]);
+    e->inflight.erase(e->inflight.begin() + (std::ptrdiff_t)i);
     Slot &sl = e->slots[rd.slot];
     float ms = 0;
     cudaEventElapsedTime(&ms, sl.ev0, sl.ev1);
     sl.busy = false;
     e->st.rounds++;
     e->st.gpu_seconds += ms * 1e-3;
+    e->st.walk_steps += *(volatile unsigned long long *)sl.steps_host;
     if (ms > 0.05f) {
         double f = std::min(2.0, std::max(0.5, e->round_seconds * 1e3 / ms));
         e->round_budget_steps = std::min(2e10, std::max(1e5, e->round_budget_steps * f));
@@ -293,7 +307,9 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
         }
     }
     if (!sl.counters.p) {
-        if ((er = sl.counters.alloc(3 * 8)) != cudaSuccess) return er;
+        if ((er = sl.counters.alloc(4 * 8)) != cudaSuccess) return er;
+        if ((er = cudaMallocHost((void **)&sl.steps_host, 8)) != cudaSuccess) return er;
+        *sl.steps_host = 0;
         rebuild = true;
     }
     if (!rebuild) return cudaSuccess;
@@ -305,31 +321,32 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
     for (int di = 0; di < 2; ++di)
         if ((er = batch_grid(di + 2, e->block, sl.depth[di], &blocks[di])) != cudaSuccess) return er;
     unsigned long long *ctr = (unsigned long long *)sl.counters.p;
-    if ((er = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return er;
-    cudaMemsetAsync(sl.counters.p, 0, 3 * 8, e->stream);
+    if ((er = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return er;
+    cudaMemsetAsync(sl.counters.p, 0, 4 * 8, sl.stream);
     for (int di = 0; di < 2; ++di)
-        cudaMemcpyAsync(sl.jobs[di].p, sl.host[di], table_bytes(sl.cap[di]), cudaMemcpyHostToDevice, e->stream);
+        cudaMemcpyAsync(sl.jobs[di].p, sl.host[di], table_bytes(sl.cap[di]), cudaMemcpyHostToDevice, sl.stream);
     // the 2D and 3D kernels are parallel branches of the graph (the 3D one
     // on the side stream, forked and joined inside the capture), so each
     // fills the SMs the other's tail leaves idle
-    cudaEventRecord(e->ev_fork, e->stream);
-    cudaStreamWaitEvent(e->side, e->ev_fork, 0);
+    cudaEventRecord(sl.fork, sl.stream);
+    cudaStreamWaitEvent(sl.side, sl.fork, 0);
     for (int di = 0; di < 2; ++di) {
         const unsigned char *base = (const unsigned char *)sl.jobs[di].p;
         launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)), ctr + di,
                           (unsigned int *)(ctr + 2), sl.depth[di], nullptr, e->block, blocks[di],
-                          di == 0 ? e->stream : e->side);
+                          di == 0 ? sl.stream : sl.side, ctr + 3);
     }
-    cudaEventRecord(e->ev_join, e->side);
-    cudaStreamWaitEvent(e->stream, e->ev_join, 0);
-    er = cudaStreamEndCapture(e->stream, &sl.graph);
+    cudaEventRecord(sl.join, sl.side);
+    cudaStreamWaitEvent(sl.stream, sl.join, 0);
+    cudaMemcpyAsync(sl.steps_host, ctr + 3, 8, cudaMemcpyDeviceToHost, sl.stream);
+    er = cudaStreamEndCapture(sl.stream, &sl.graph);
     if (er != cudaSuccess) return er;
     return cudaGraphInstantiate(&sl.exec, sl.graph, 0);
 }
 
 bool launch_round(wost_engine *e) {
     int si = -1;
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < kSlots; ++i)
         if (!e->slots[i].busy) {
             si = i;
             break;
@@ -417,12 +434,15 @@ bool launch_round(wost_engine *e) {
         BatchHeader hd{(int)cnt[di], 0, total[di]};
         std::memcpy(sl.host[di], &hd, sizeof hd);
     }
-    cudaEventRecord(sl.ev0, e->stream);
-    err = cudaGraphLaunch(sl.exec, e->stream);
-    cudaEventRecord(sl.ev1, e->stream);
+    // the round runs after the admissions (buffer set-up) issued before it
+    err = cudaEventRecord(e->ev_ready, e->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sl.stream, e->ev_ready, 0);
+    if (err == cudaSuccess) err = cudaEventRecord(sl.ev0, sl.stream);
+    if (err == cudaSuccess) err = cudaGraphLaunch(sl.exec, sl.stream);
+    if (err == cudaSuccess) err = cudaEventRecord(sl.ev1, sl.stream);
     if (err != cudaSuccess) {
         for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_CUDA);
-        cudaStreamSynchronize(e->stream);
+        cudaStreamSynchronize(sl.stream);
         return false;
     }
     e->st.graph_launches++;
@@ -435,20 +455,18 @@ void engine_loop(wost_engine *e) {
     cudaSetDevice(e->device);
     std::unique_lock<std::mutex> lk(e->mu);
     for (;;) {
-        while (!e->inflight.empty() && cudaEventQuery(e->slots[e->inflight.front().slot].ev1) != cudaErrorNotReady)
-            retire_front(e);
+        // rounds on different streams may finish in any order
+        for (size_t i = 0; i < e->inflight.size();) {
+            if (cudaEventQuery(e->slots[e->inflight[i].slot].ev1) != cudaErrorNotReady) retire(e, i);
+            else ++i;
+        }
         process_cancels(e);
         if (e->stop && e->inflight.empty()) break;
         if (!e->stop) admit(e);
-        if (!e->stop && e->inflight.size() < 2 && launch_round(e)) continue;
-        if (!e->inflight.empty()) {
-            cudaEvent_t ev = e->slots[e->inflight.front().slot].ev1;
-            lk.unlock();
-            cudaEventSynchronize(ev);
-            lk.lock();
-        } else {
-            e->cv.wait_for(lk, std::chrono::milliseconds(2));
-        }
+        if (!e->stop && (int)e->inflight.size() < kSlots && launch_round(e)) continue;
+        // nothing to launch: wake on a submission or cancellation, or poll
+        // the rounds in flight again after a short sleep
+        e->cv.wait_for(lk, std::chrono::milliseconds(e->inflight.empty() ? 2 : 1));
     }
     // stopped: whatever is left is cancelled
     std::vector<Request *> left(e->active.begin(), e->active.end());
@@ -515,13 +533,17 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
             CK(batch_grid(3, block, 64, &blocks3), "occupancy");
             e->min_round_steps = 4.0 * 64.0 * (double)blocks3 * block;
         }
+        int prio_low = 0, prio_high = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
         CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        CK(cudaStreamCreateWithFlags(&e->check_stream, cudaStreamNonBlocking), "cudaStreamCreate");
-        CK(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking), "cudaStreamCreate");
-        CK(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
-        CK(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaStreamCreateWithPriority(&e->check_stream, cudaStreamNonBlocking, prio_high), "cudaStreamCreate");
         CK(cudaEventCreateWithFlags(&e->ev_admit, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_ready, cudaEventDisableTiming), "cudaEventCreate");
         for (auto &s : e->slots) {
+            CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            CK(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking), "cudaStreamCreate");
+            CK(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming), "cudaEventCreate");
+            CK(cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming), "cudaEventCreate");
             CK(cudaEventCreate(&s.ev0), "cudaEventCreate");
             CK(cudaEventCreate(&s.ev1), "cudaEventCreate");
         }
@@ -640,23 +662,19 @@ wost_status wost_engine_destroy(wost_engine *e) {
     if (e->th.joinable()) e->th.join();
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->stream);
+    for (auto &s : e->slots)
+        if (s.stream) cudaStreamSynchronize(s.stream);
     for (auto &kv : e->by_handle) {
         kv.first->engine = nullptr;  // the handle outlives the engine
         delete kv.second;
     }
     e->by_handle.clear();
-    for (auto &s : e->slots) {
-        if (s.ev0) cudaEventDestroy(s.ev0);
-        if (s.ev1) cudaEventDestroy(s.ev1);
-    }
     if (e->stat_host) cudaFreeHost(e->stat_host);
     cudaStreamDestroy(e->check_stream);
-    cudaEventDestroy(e->ev_fork);
-    cudaEventDestroy(e->ev_join);
     cudaEventDestroy(e->ev_admit);
-    cudaStreamDestroy(e->side);
+    cudaEventDestroy(e->ev_ready);
     cudaStreamDestroy(e->stream);
-    delete e;
+    delete e;  // the slots release their graphs, streams and events
     return WOST_OK;
 }
 

@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "wost_screened.cuh"
-#include "wost_walk.cuh"
+#include "wost_batch.cuh"
 
 namespace wost {
 
@@ -68,12 +68,12 @@ cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
 
 cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
                               unsigned int *guard, int depth, const int *cancel, int block, int blocks,
-                              cudaStream_t s) {
+                              cudaStream_t s, unsigned long long *steps_out) {
     size_t sm = smem_bytes(depth, block);
     if (dim == 2)
-        k_walk_batch<2><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
+        k_walk_batch<2><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel, steps_out);
     else
-        k_walk_batch<3><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel);
+        k_walk_batch<3><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel, steps_out);
     return cudaGetLastError();
 }
 

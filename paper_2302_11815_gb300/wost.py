@@ -26,7 +26,7 @@ STATUS_NAMES = ["OK", "INVALID_ARG", "OUT_OF_MEMORY", "BUDGET", "CUDA", "TIMEOUT
 DATA = {"none": 0, "per_vertex": 1, "per_corner": 2, "analytic": 3, "grid": 4}
 FN = {"zero": 0, "exp_cos": 1, "sin2x_cos3y": 2, "quad3": 3, "bump": 4, "linear": 5, "log_radial": 6,
       "exp_plane": 7}
-ABI_VERSION = 3  # WOST_ABI_VERSION of the header these structures mirror
+ABI_VERSION = 4  # WOST_ABI_VERSION of the header these structures mirror
 MEM_HOST, MEM_DEVICE = 0, 1
 KERNEL = {"plain": 0, "persistent": 1, "counting": 2, "resumable": 3}
 COUNT_NAMES = ("q1", "q2", "q3", "q4", "vis")
@@ -309,7 +309,8 @@ class wost_engine_stats(C.Structure):
                 ("cancelled", C.c_uint64), ("rejected", C.c_uint64), ("capped", C.c_uint64), ("queued", C.c_int32),
                 ("active", C.c_int32), ("rounds", C.c_uint64), ("graph_launches", C.c_uint64),
                 ("gpu_seconds", C.c_double),
-                ("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("round_budget_steps", C.c_double)]
+                ("budget_bytes", C.c_int64), ("used_bytes", C.c_int64), ("round_budget_steps", C.c_double),
+                ("walk_steps", C.c_uint64)]
 
 
 def wost_engine_create(device=0, memory_budget_bytes=0, round_seconds=0.0, min_walks=0, max_walks_per_point=0,

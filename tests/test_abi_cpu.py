@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(lib):
     cdll = C.CDLL(wost.LIBPATH)
     missing = [n for n in declared_functions() if not hasattr(cdll, n)]
     assert not missing, missing
-    assert wost.wost_abi_version() == wost.ABI_VERSION == 3
+    assert wost.wost_abi_version() == wost.ABI_VERSION == 4
 
 
 STRUCTS = ("wost_field", "wost_scene_desc", "wost_scene_info", "wost_solve_desc", "wost_progress",

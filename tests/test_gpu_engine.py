@@ -100,6 +100,8 @@ def test_engine_results_same_alone_and_in_the_mix(wost, mix):
         alone.append(r[0])
     both, stats = _run_engine(wost, S, specs, targets, [100, 101, 102], caps, round_seconds=0.005)
     assert stats["completed"] == 3 and stats["rounds"] >= 3
+    # the rounds' device count of walk steps is the requests' own, walk for walk
+    assert stats["walk_steps"] == sum(int(r[3]["total_steps"]) for r in both)
     for i in range(3):
         m_a, se_a, w_a, _ = alone[i]
         m_b, se_b, w_b, _ = both[i]
