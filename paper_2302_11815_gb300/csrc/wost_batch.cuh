@@ -1,6 +1,7 @@
 // The batched persistent walk kernel (wost_solve_batch and the serving
-// engine's rounds), instantiated in the screened translation unit
-// (wost_kernels_scr.cu): every walk of a batch may belong to a screened solve.
+// engine's rounds), instantiated in wost_kernels_batch.cu in two forms:
+// SCR = true when a job of the batch is screened, SCR = false (the smaller
+// Poisson-only code) when none is.
 #pragma once
 
 #include "wost_walk.cuh"
@@ -12,7 +13,7 @@ namespace wost {
 // the jobs' walks; a team maps its next index to a job by binary search over
 // the jobs' first indices and runs that job's walk on that job's scene.
 // steps_out (may be null) receives the walk steps of the finished walks.
-template <int D>
+template <int D, bool SCR>
 __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hdr,
                                                     const BatchJob *__restrict__ jobs, unsigned long long *counter,
                                                     unsigned int *guard, int stack_depth, const int *cancel,
@@ -68,7 +69,7 @@ __global__ void WOST_WALK_BOUNDS k_walk_batch(const BatchHeader *__restrict__ hd
         if (!__any_sync(FULL, job >= 0 || !drained)) break;
         // lanes without a job step a dummy reference to job 0 (inactive)
         const BatchJob &J = jobs[job >= 0 ? job : 0];
-        if (walk_step<D, true>(*J.scene, J.sp, w, q, job >= 0)) {
+        if (walk_step<D, SCR>(*J.scene, J.sp, w, q, job >= 0)) {
             if (g.leader()) {
                 accumulate(J.acc, w);
                 ran += (unsigned int)w.steps;

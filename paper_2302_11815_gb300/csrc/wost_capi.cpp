@@ -4,6 +4,7 @@
 // thread-local message and returns a status.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -498,8 +499,11 @@ wost_status wost_solve_batch(int32_t n, wost_scene *const *scenes, const wost_so
             CK(batch_grid(di + 2, block, depth[di], &blocks), "occupancy");
             const unsigned char *base = (const unsigned char *)shared->jobs[di].p;
             cudaStream_t ls = (both && di == 1) ? shared->side : stream;
+            const bool scr = std::any_of(jobs[di].begin(), jobs[di].end(),
+                                         [](const BatchJob &j) { return j.sp.sigma > 0.f; });
             CK(launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)),
-                                 ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, ls),
+                                 ctr + di, (unsigned int *)(ctr + 2), depth[di], nullptr, block, blocks, ls, nullptr,
+                                 scr),
                "kernel launch");
         }
         if (both) {

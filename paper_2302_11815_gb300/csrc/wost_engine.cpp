@@ -12,7 +12,10 @@
 // rounds while the GPU runs earlier ones.  Requests are admitted FIFO by
 // device-memory budget, run in stages of walks per point, and are checked
 // after each stage with the per-solve summary kernel (k_request_stats) on a
-// high-priority stream (its blocks go first when SMs free up).
+// high-priority stream (its blocks go first when SMs free up).  A check is
+// asynchronous: the scheduler issues it and reads its results once its event
+// has completed, so it never waits for the device with the engine's lock
+// held (submissions and new rounds go on meanwhile).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -65,6 +68,7 @@ struct Slot {
     unsigned char *host[2] = {nullptr, nullptr};
     size_t cap[2] = {0, 0};    // jobs per table
     int depth[2] = {0, 0};     // stack entries the graph was captured with
+    bool scr[2] = {true, true};  // the kernels' form: screened, or Poisson only
     DevBuf counters;           // next walk 2D, next walk 3D, guard, walk steps run
     unsigned long long *steps_host = nullptr;  // pinned copy of the walk-step count
     cudaGraph_t graph = nullptr;
@@ -95,6 +99,27 @@ struct Round {
     std::vector<Piece> pieces;
 };
 
+// One stage check in flight: the summary kernel's inputs and outputs for the
+// requests whose stage completed, on the device and in pinned host memory.
+// Outputs, cap entries each: max variance (FP32 bits, u32), then min walks,
+// steps and walks (u64) at byte offsets 8, 16 and 24 times cap.
+struct CheckSet {
+    DevBuf jobs, out;
+    StatJob *host_jobs = nullptr;
+    unsigned char *host_out = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    std::vector<Request *> reqs;
+    bool busy = false;
+    ~CheckSet() {
+        if (host_jobs) cudaFreeHost(host_jobs);
+        if (host_out) cudaFreeHost(host_out);
+        if (ev) cudaEventDestroy(ev);
+    }
+};
+
+constexpr int kChecks = 4;  // stage checks in flight at most
+
 }  // namespace
 
 struct wost_engine {
@@ -118,9 +143,8 @@ struct wost_engine {
     wost_engine_stats st{};
     bool stop = false;
     std::thread th;
-    DevBuf stat_jobs, stat_out;
-    StatJob *stat_host = nullptr;
-    size_t stat_cap = 0;
+    CheckSet checks[kChecks];
+    std::deque<int> check_order;  // busy check sets, oldest first
 };
 
 namespace {
@@ -186,45 +210,16 @@ void admit(wost_engine *e) {
     }
 }
 
-// Stage checks of the requests whose current stage has fully completed.
-void check_stages(wost_engine *e, std::vector<Request *> &ready) {
-    if (ready.empty()) return;
-    size_t n = ready.size();
-    if (n > e->stat_cap) {
-        if (e->stat_host) cudaFreeHost(e->stat_host);
-        e->stat_cap = std::max<size_t>(n, 2 * e->stat_cap);
-        cudaMallocHost((void **)&e->stat_host, e->stat_cap * (sizeof(StatJob) + 32));
-        e->stat_jobs.~DevBuf();
-        new (&e->stat_jobs) DevBuf();
-        e->stat_out.~DevBuf();
-        new (&e->stat_out) DevBuf();
-        e->stat_jobs.alloc(e->stat_cap * sizeof(StatJob));
-        e->stat_out.alloc(e->stat_cap * 32);
-    }
-    int64_t maxn = 0;
-    for (size_t i = 0; i < n; ++i) {
-        const Accumulators &a = ready[i]->h->acc;
-        e->stat_host[i] = StatJob{a.sum, a.sumsq, a.walks, a.steps, ready[i]->h->n_points};
-        maxn = std::max(maxn, ready[i]->h->n_points);
-    }
-    unsigned char *out = (unsigned char *)e->stat_out.p;
-    unsigned int *mvar = (unsigned int *)out;                                  // [n]
-    unsigned long long *minw = (unsigned long long *)(out + 8 * e->stat_cap);  // [n]
-    unsigned long long *ssum = minw + e->stat_cap, *wsum = ssum + e->stat_cap;
-    cudaMemcpyAsync(e->stat_jobs.p, e->stat_host, n * sizeof(StatJob), cudaMemcpyHostToDevice, e->check_stream);
-    cudaMemsetAsync(mvar, 0, n * 4, e->check_stream);
-    cudaMemsetAsync(minw, 0xFF, n * 8, e->check_stream);
-    cudaMemsetAsync(ssum, 0, n * 8, e->check_stream);
-    cudaMemsetAsync(wsum, 0, n * 8, e->check_stream);
-    launch_request_stats((const StatJob *)e->stat_jobs.p, (int)n, maxn, mvar, minw, ssum, wsum, e->check_stream);
-    std::vector<unsigned int> hv(n);
-    std::vector<unsigned long long> hs(n), hw(n);
-    cudaMemcpyAsync(hv.data(), mvar, n * 4, cudaMemcpyDeviceToHost, e->check_stream);
-    cudaMemcpyAsync(hs.data(), ssum, n * 8, cudaMemcpyDeviceToHost, e->check_stream);
-    cudaMemcpyAsync(hw.data(), wsum, n * 8, cudaMemcpyDeviceToHost, e->check_stream);
-    cudaError_t err = cudaStreamSynchronize(e->check_stream);
-    for (size_t i = 0; i < n; ++i) {
-        Request *r = ready[i];
+// Stage decisions from a completed check: finish the request (target met,
+// walk cap reached, cancelled) or size its next stage from its variance.
+void apply_check(wost_engine *e, CheckSet &cs, cudaError_t err) {
+    const size_t cap = cs.cap;
+    const unsigned int *hv = (const unsigned int *)cs.host_out;
+    const unsigned long long *hs = (const unsigned long long *)(cs.host_out + 16 * cap);
+    const unsigned long long *hw = (const unsigned long long *)(cs.host_out + 24 * cap);
+    for (size_t i = 0; i < cs.reqs.size(); ++i) {
+        Request *r = cs.reqs[i];
+        r->outstanding--;
         if (err != cudaSuccess) {
             finish(e, r, WOST_ERR_CUDA);
             continue;
@@ -248,6 +243,86 @@ void check_stages(wost_engine *e, std::vector<Request *> &ready) {
             r->cursor = 0;
         }
     }
+    cs.reqs.clear();
+    cs.busy = false;
+}
+
+// Applies the checks whose results have arrived (all of them, waiting for
+// the device, if wait is set).
+void complete_checks(wost_engine *e, bool wait) {
+    while (!e->check_order.empty()) {
+        CheckSet &cs = e->checks[e->check_order.front()];
+        cudaError_t q = wait ? cudaEventSynchronize(cs.ev) : cudaEventQuery(cs.ev);
+        if (q == cudaErrorNotReady) return;
+        e->check_order.pop_front();
+        apply_check(e, cs, q);
+    }
+}
+
+// Issues the stage check of the requests whose current stage has fully
+// completed; each counts as outstanding until its check is applied.
+void issue_check(wost_engine *e, std::vector<Request *> &ready) {
+    if (ready.empty()) return;
+    int ci = -1;
+    for (int i = 0; i < kChecks && ci < 0; ++i)
+        if (!e->checks[i].busy) ci = i;
+    if (ci < 0) {  // all sets in flight: the oldest is applied first
+        int oldest = e->check_order.front();
+        CheckSet &o = e->checks[oldest];
+        cudaError_t q = cudaEventSynchronize(o.ev);
+        e->check_order.pop_front();
+        apply_check(e, o, q);
+        ci = oldest;
+    }
+    CheckSet &cs = e->checks[ci];
+    const size_t n = ready.size();
+    cudaError_t err = cudaSuccess;
+    if (n > cs.cap) {
+        size_t nc = std::max<size_t>(n, 2 * cs.cap);
+        if (cs.host_jobs) cudaFreeHost(cs.host_jobs);
+        if (cs.host_out) cudaFreeHost(cs.host_out);
+        cs.host_jobs = nullptr;
+        cs.host_out = nullptr;
+        cs.cap = 0;
+        cs.jobs.release_async(e->check_stream);
+        cs.out.release_async(e->check_stream);
+        if ((err = cudaMallocHost((void **)&cs.host_jobs, nc * sizeof(StatJob))) == cudaSuccess &&
+            (err = cudaMallocHost((void **)&cs.host_out, nc * 32)) == cudaSuccess &&
+            (err = cs.jobs.alloc_async(nc * sizeof(StatJob), e->check_stream)) == cudaSuccess &&
+            (err = cs.out.alloc_async(nc * 32, e->check_stream)) == cudaSuccess)
+            cs.cap = nc;
+    }
+    if (err == cudaSuccess && !cs.ev) err = cudaEventCreateWithFlags(&cs.ev, cudaEventDisableTiming);
+    if (err != cudaSuccess) {
+        for (Request *r : ready) finish(e, r, WOST_ERR_CUDA);
+        return;
+    }
+    const size_t cap = cs.cap;
+    int64_t maxn = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const Accumulators &a = ready[i]->h->acc;
+        cs.host_jobs[i] = StatJob{a.sum, a.sumsq, a.walks, a.steps, ready[i]->h->n_points};
+        maxn = std::max(maxn, ready[i]->h->n_points);
+    }
+    unsigned char *out = (unsigned char *)cs.out.p;
+    unsigned int *mvar = (unsigned int *)out;
+    unsigned long long *minw = (unsigned long long *)(out + 8 * cap);
+    unsigned long long *ssum = minw + cap, *wsum = ssum + cap;
+    cudaStream_t s = e->check_stream;
+    cudaMemcpyAsync(cs.jobs.p, cs.host_jobs, n * sizeof(StatJob), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(mvar, 0, n * 4, s);
+    cudaMemsetAsync(minw, 0xFF, n * 8, s);
+    cudaMemsetAsync(ssum, 0, n * 8, s);
+    cudaMemsetAsync(wsum, 0, n * 8, s);
+    launch_request_stats((const StatJob *)cs.jobs.p, (int)n, maxn, mvar, minw, ssum, wsum, s);
+    cudaMemcpyAsync(cs.host_out, mvar, n * 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(cs.host_out + 16 * cap, ssum, n * 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(cs.host_out + 24 * cap, wsum, n * 8, cudaMemcpyDeviceToHost, s);
+    cudaEventRecord(cs.ev, s);
+    cs.reqs = ready;
+    for (Request *r : ready) r->outstanding++;
+    cs.busy = true;
+    e->check_order.push_back(ci);
 }
 
 void retire(wost_engine *e, size_t i) {
@@ -272,7 +347,7 @@ void retire(wost_engine *e, size_t i) {
             std::find(ready.begin(), ready.end(), p.r) == ready.end())
             ready.push_back(p.r);
     }
-    check_stages(e, ready);
+    issue_check(e, ready);
 }
 
 void process_cancels(wost_engine *e) {
@@ -283,8 +358,9 @@ void process_cancels(wost_engine *e) {
 }
 
 // (Re)captures the slot's round graph if its tables are too small for this
-// round or a scene needs a deeper stack than the graph was captured with.
-cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const int depth[2]) {
+// round, a scene needs a deeper stack than the graph was captured with, or
+// the round needs the other kernel form (a screened job, or none).
+cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const int depth[2], const bool scr[2]) {
     bool rebuild = sl.exec == nullptr;
     cudaError_t er;
     for (int di = 0; di < 2; ++di) {
@@ -303,6 +379,10 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
         int want = std::max(depth[di], 2);
         if (want > sl.depth[di]) {
             sl.depth[di] = want;
+            rebuild = true;
+        }
+        if (cnt[di] && scr[di] != sl.scr[di]) {
+            sl.scr[di] = scr[di];
             rebuild = true;
         }
     }
@@ -334,7 +414,7 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
         const unsigned char *base = (const unsigned char *)sl.jobs[di].p;
         launch_walk_batch(di + 2, (const BatchHeader *)base, (const BatchJob *)(base + sizeof(BatchHeader)), ctr + di,
                           (unsigned int *)(ctr + 2), sl.depth[di], nullptr, e->block, blocks[di],
-                          di == 0 ? sl.stream : sl.side, ctr + 3);
+                          di == 0 ? sl.stream : sl.side, ctr + 3, sl.scr[di]);
     }
     cudaEventRecord(sl.join, sl.side);
     cudaStreamWaitEvent(sl.stream, sl.join, 0);
@@ -401,12 +481,14 @@ bool launch_round(wost_engine *e) {
     Slot &sl = e->slots[si];
     size_t cnt[2] = {0, 0};
     int depth[2] = {0, 0};
+    bool scr[2] = {false, false};
     for (auto &p : rd.pieces) {
         int di = p.r->h->dim - 2;
         cnt[di]++;
         depth[di] = std::max(depth[di], p.r->scene->stack_depth);
+        scr[di] = scr[di] || p.r->h->sp.sigma > 0.f;
     }
-    cudaError_t err = ensure_graph(e, sl, cnt, depth);
+    cudaError_t err = ensure_graph(e, sl, cnt, depth, scr);
     if (err != cudaSuccess) {
         for (auto &p : rd.pieces) finish(e, p.r, WOST_ERR_CUDA);
         return false;
@@ -460,8 +542,9 @@ void engine_loop(wost_engine *e) {
             if (cudaEventQuery(e->slots[e->inflight[i].slot].ev1) != cudaErrorNotReady) retire(e, i);
             else ++i;
         }
+        complete_checks(e, false);
         process_cancels(e);
-        if (e->stop && e->inflight.empty()) break;
+        if (e->stop && e->inflight.empty() && e->check_order.empty()) break;
         if (!e->stop) admit(e);
         if (!e->stop && (int)e->inflight.size() < kSlots && launch_round(e)) continue;
         // nothing to launch: wake on a submission or cancellation, or poll
@@ -669,7 +752,7 @@ wost_status wost_engine_destroy(wost_engine *e) {
         delete kv.second;
     }
     e->by_handle.clear();
-    if (e->stat_host) cudaFreeHost(e->stat_host);
+    cudaStreamSynchronize(e->check_stream);
     cudaStreamDestroy(e->check_stream);
     cudaEventDestroy(e->ev_admit);
     cudaEventDestroy(e->ev_ready);

@@ -18,7 +18,7 @@ cudaError_t launch_request_stats(const StatJob *jobs, int n_jobs, int64_t max_po
                                  unsigned long long *walks_sum, cudaStream_t s);
 cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
                               unsigned int *guard, int depth, const int *cancel, int block, int blocks,
-                              cudaStream_t s, unsigned long long *steps_out = nullptr);
+                              cudaStream_t s, unsigned long long *steps_out = nullptr, bool screened = true);
 // lanes: lanes per walk, 1 (binary trees) or 8 (8-lane teams over the 8-wide
 // trees; Poisson solves)
 cudaError_t launch_walk_persistent(const SceneView &sc, const SolveParams &sp, const Accumulators &acc, int block,

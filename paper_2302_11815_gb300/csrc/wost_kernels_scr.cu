@@ -1,11 +1,10 @@
 // Screened walk kernels (the SCR = true instantiations of wost_walk.cuh:
-// -Lap u + sigma u = f, App. A.2), the batched kernel (whose jobs may be
-// screened or not), the evaluation kernel of the screened Green's function
-// and step weight, and their launchers (sm_103a).
+// -Lap u + sigma u = f, App. A.2), the evaluation kernel of the screened
+// Green's function and step weight, and their launchers (sm_103a).
 #include <cuda_runtime.h>
 
 #include "wost_screened.cuh"
-#include "wost_batch.cuh"
+#include "wost_walk.cuh"
 
 namespace wost {
 
@@ -48,33 +47,6 @@ cudaError_t launch_walk_persistent_scr(const SceneView &sc, const SolveParams &s
 cudaError_t launch_walk_resume_scr(const SceneView &sc, const SolveParams &sp, const Accumulators &acc,
                                    const ResumeState &rs, int iters, int block, int blocks, cudaStream_t s) {
     return walk_resume_launch<true, 1>(sc, sp, acc, rs, iters, block, blocks, s);
-}
-
-cudaError_t batch_grid(int dim, int block, int depth, int *blocks_out) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t sm = smem_bytes(depth, block);
-    if (e == cudaSuccess && sm > 48 * 1024)
-        e = dim == 2 ? cudaFuncSetAttribute(k_walk_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                     : cudaFuncSetAttribute(k_walk_batch<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<2>, block, sm)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch<3>, block, sm);
-    if (e != cudaSuccess) return e;
-    *blocks_out = sms * (per_sm > 0 ? per_sm : 1);
-    return cudaSuccess;
-}
-
-cudaError_t launch_walk_batch(int dim, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *counter,
-                              unsigned int *guard, int depth, const int *cancel, int block, int blocks,
-                              cudaStream_t s, unsigned long long *steps_out) {
-    size_t sm = smem_bytes(depth, block);
-    if (dim == 2)
-        k_walk_batch<2><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel, steps_out);
-    else
-        k_walk_batch<3><<<blocks, block, sm, s>>>(hdr, jobs, counter, guard, depth, cancel, steps_out);
-    return cudaGetLastError();
 }
 
 }  // namespace wost

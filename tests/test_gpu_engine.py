@@ -72,6 +72,30 @@ def test_batch_equals_solves_alone(wost, mix):
         assert got[i][3]["done"] == 1 and int(got[i][2].sum()) == len(sc["points"]) * walks[i]
 
 
+def test_batch_with_a_screened_job_equals_solves_alone(wost, mix):
+    """A batch holding a screened job runs the screened form of the batched
+    kernel for its dimension (the Poisson-only form for the other): every
+    job's result is still its result alone."""
+    specs, S = mix
+    walks, sig = [32, 16, 24], [0.5, 0.0, 2.0]
+    reqs = [dict(points=torch.from_numpy(sc["points"]).cuda(), walks_per_point=w, epsilon=sc["epsilon"],
+                 r_min=sc["r_min"], max_steps=sc["max_steps"], seed=40 + i, sigma=g)
+            for i, (sc, w, g) in enumerate(zip(specs, walks, sig))]
+    hs = wost.wost_solve_batch([s.handle for s in S], reqs)
+    try:
+        for h in hs:
+            wost.wost_wait(h, 300)
+        got = [wost.wost_poll(h, len(sc["points"])) for h, sc in zip(hs, specs)]
+    finally:
+        for h in hs:
+            wost.wost_solve_destroy(h)
+    for i, (sc, s) in enumerate(zip(specs, S)):
+        ref = wost.solve(s, torch.from_numpy(sc["points"]).cuda(), walks[i], sc["epsilon"], sc["r_min"],
+                         sc["max_steps"], seed=40 + i, kernel="persistent", sigma=sig[i])
+        np.testing.assert_allclose(got[i][0], ref["mean"], **FP32_WALKS)
+        assert got[i][3]["total_steps"] == ref["total_steps"]
+
+
 def _run_engine(wost, S, specs, targets, seeds, caps, **kw):
     eng = wost.wost_engine_create(**kw)
     hs = []
