@@ -80,21 +80,19 @@ static __device__ __noinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
 // One out-of-line copy of each library function the walk step needs.  Inlined
 // at every call site, their range reductions and slow paths were a fifth of
 // the walk kernels' code, and instruction supply is what stalls those
-// kernels most (ncu: no_instruction the leading stall reason).
+// kernels most (ncu: no_instruction the leading stall reason).  Results come
+// back by value: an out-of-line function writing through pointers would put
+// the caller's variables in local memory.
 static __device__ __noinline__ float m_exp(float a) { return expf(a); }
 static __device__ __noinline__ float m_log(float a) { return logf(a); }
 static __device__ __noinline__ float m_asin(float a) { return asinf(a); }
-static __device__ __noinline__ void m_sincos(float a, float *s, float *c) { sincosf(a, s, c); }
-__device__ __forceinline__ float m_sin(float a) {
+static __device__ __noinline__ float2 m_sincos(float a) {
     float s, c;
-    m_sincos(a, &s, &c);
-    return s;
+    sincosf(a, &s, &c);
+    return make_float2(s, c);
 }
-__device__ __forceinline__ float m_cos(float a) {
-    float s, c;
-    m_sincos(a, &s, &c);
-    return c;
-}
+__device__ __forceinline__ float m_sin(float a) { return m_sincos(a).x; }
+__device__ __forceinline__ float m_cos(float a) { return m_sincos(a).y; }
 
 // (0,1): top 23 bits plus one half, times 2^-23 (exact in FP32)
 __device__ __forceinline__ float u01(uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); }
@@ -110,7 +108,9 @@ struct Stream {  // sequential uniforms from slots 1, 2, ... of one (walk, point
         k1 = key1;
         used = 4;
     }
-    __device__ __noinline__ float next() {  // one copy: ~14 draws per step from 4 call sites
+    // inline (the refill calls the one out-of-line Philox): an out-of-line
+    // member function would keep the stream's state in local memory
+    __device__ __forceinline__ float next() {
         if (used == 4) {
             buf = philox10(ctr, k0, k1);
             ctr.w += 1u;
@@ -737,6 +737,11 @@ __device__ __noinline__ int q_ray2(const TreeView &T, P3 o, P3 va, float tmaxA, 
 // far, which is never below the true minimum, so postponing a leaf only
 // visits some nodes a tighter bound would have pruned (the postponed
 // traversal of Aila & Laine, HPG 2009, for nearest-point and ray queries).
+// The visitors' methods are all inlined: a visitor whose method stays out of
+// line must live in addressable memory, and as it refers to the kernel's
+// scene parameter, the compiler then copies ~800 bytes of kernel parameters
+// into every thread's local memory (measured: 2D walk kernels 960 -> 96 bytes
+// of stack frame, 4.6% more walk steps/s on the Koch workload).
 template <class V>
 __device__ __forceinline__ bool spop_keep(const Stack &st, int &sp, uint32_t &ref, const V &vis) {
     while (sp > 0) {
@@ -797,16 +802,16 @@ struct ClosestVisitor {  // Q.1
     P3 x;
     Closest best;
     Cnt<CN> &cnt;
-    __device__ bool keep(float key) const { return key < best.d2; }
-    __device__ bool first0(float k0, float k1) const { return k0 <= k1; }
-    __device__ void count_node() { cnt.node(C_Q1); }
-    __device__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
+    __device__ __forceinline__ bool keep(float key) const { return key < best.d2; }
+    __device__ __forceinline__ bool first0(float k0, float k1) const { return k0 <= k1; }
+    __device__ __forceinline__ void count_node() { cnt.node(C_Q1); }
+    __device__ __forceinline__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
         k0 = box_dist2<D>(n.lo0, n.hi0, x);
         k1 = box_dist2<D>(n.lo1, n.hi1, x);
         h0 = k0 < best.d2;
         h1 = k1 < best.d2;
     }
-    __device__ void leaf(uint32_t f, uint32_t c) {
+    __device__ __forceinline__ void leaf(uint32_t f, uint32_t c) {
         for (uint32_t k = f; k < f + c; ++k) {
             cnt.prim(C_Q1);
             Prim<D> p = load_prim<D>(T.prims, k);
@@ -844,10 +849,10 @@ struct SilhouetteVisitor {  // Q.2
     float r2;
     bool found;
     Cnt<CN> &cnt;
-    __device__ bool keep(float key) const { return key < r2; }
-    __device__ bool first0(float k0, float k1) const { return k0 <= k1; }
-    __device__ void count_node() { cnt.node(C_Q2); }
-    __device__ void children(const Node<D> &n, uint32_t ref, bool &h0, bool &h1, float &k0, float &k1) const {
+    __device__ __forceinline__ bool keep(float key) const { return key < r2; }
+    __device__ __forceinline__ bool first0(float k0, float k1) const { return k0 <= k1; }
+    __device__ __forceinline__ void count_node() { cnt.node(C_Q2); }
+    __device__ __forceinline__ void children(const Node<D> &n, uint32_t ref, bool &h0, bool &h1, float &k0, float &k1) const {
         k0 = box_dist2<D>(n.lo0, n.hi0, x);
         k1 = box_dist2<D>(n.lo1, n.hi1, x);
         h0 = k0 < r2;
@@ -855,7 +860,7 @@ struct SilhouetteVisitor {  // Q.2
         if (h0 && k0 > 0.f) h0 = has_silhouette<D>(n.lo0, n.hi0, load_cone<D>(T.cones, ref, 0), x);
         if (h1 && k1 > 0.f) h1 = has_silhouette<D>(n.lo1, n.hi1, load_cone<D>(T.cones, ref, 1), x);
     }
-    __device__ void leaf(uint32_t f, uint32_t c) {
+    __device__ __forceinline__ void leaf(uint32_t f, uint32_t c) {
         for (uint32_t k = f; k < f + c; ++k) {
             cnt.prim(C_Q2);
             float d2 = sil_test<D>(T.prims, k, x, r2);
@@ -887,10 +892,10 @@ struct Ray2Visitor {  // Q.3 (ray A) and the visibility of the Neumann sample (r
     int skipB, hit;
     bool actB, occB;
     Cnt<CN> &cnt;
-    __device__ bool keep(float key) const { return fabsf(key) <= tb || (actB && signbit(key)); }
-    __device__ bool first0(float k0, float k1) const { return fabsf(k0) <= fabsf(k1); }
-    __device__ void count_node() { cnt.node(C_Q3); }
-    __device__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
+    __device__ __forceinline__ bool keep(float key) const { return fabsf(key) <= tb || (actB && signbit(key)); }
+    __device__ __forceinline__ bool first0(float k0, float k1) const { return fabsf(k0) <= fabsf(k1); }
+    __device__ __forceinline__ void count_node() { cnt.node(C_Q3); }
+    __device__ __forceinline__ void children(const Node<D> &n, uint32_t, bool &h0, bool &h1, float &k0, float &k1) const {
         float a0 = box_ray<D>(n.lo0, n.hi0, o, ia, tb), a1 = box_ray<D>(n.lo1, n.hi1, o, ia, tb);
         bool b0 = actB && box_ray<D>(n.lo0, n.hi0, o, ib, tmaxB) != INFINITY;
         bool b1 = actB && box_ray<D>(n.lo1, n.hi1, o, ib, tmaxB) != INFINITY;
@@ -899,7 +904,7 @@ struct Ray2Visitor {  // Q.3 (ray A) and the visibility of the Neumann sample (r
         k0 = key_with_b(a0, b0);
         k1 = key_with_b(a1, b1);
     }
-    __device__ void leaf(uint32_t f, uint32_t c) {
+    __device__ __forceinline__ void leaf(uint32_t f, uint32_t c) {
         for (uint32_t k = f; k < f + c; ++k) {
             Prim<D> p = load_prim<D>(T.prims, k);
             float t;
@@ -1055,15 +1060,13 @@ template <int D>
 __device__ __noinline__ P3 fn_grad(int fn, const float *p, P3 x) {
     switch (fn) {
     case 1: {
-        float e = m_exp(x.x), s, c;
-        m_sincos(x.y, &s, &c);
-        return mk(e * c, -e * s, 0.f);
+        float e = m_exp(x.x);
+        float2 sc = m_sincos(x.y);
+        return mk(e * sc.y, -e * sc.x, 0.f);
     }
     case 2: {
-        float s2, c2, s3, c3;
-        m_sincos(2.f * x.x, &s2, &c2);
-        m_sincos(3.f * x.y, &s3, &c3);
-        return mk(2.f * c2 * c3, -3.f * s2 * s3, 0.f);
+        float2 a2 = m_sincos(2.f * x.x), a3 = m_sincos(3.f * x.y);
+        return mk(2.f * a2.y * a3.y, -3.f * a2.x * a3.x, 0.f);
     }
     case 3: return mk(2.f * x.x, -2.f * x.y, 0.5f);
     case 4: return x * (-1.f / D);
