@@ -583,13 +583,10 @@ def sub_serve(wost, torch, args):
                 cur = list(live)
             for item in cur:
                 h, rq, t_sub = item
-                try:
-                    wost.wost_wait(h, 0.0)
-                    status = "ok"
-                except wost.WostError as e:
-                    if e.status == wost.ERR_TIMEOUT:  # not finished yet
-                        continue
-                    status = wost.STATUS_NAMES[e.status]  # BUDGET: shed; CANCELLED
+                st = wost.wost_wait_status(h, 0.0)
+                if st == wost.ERR_TIMEOUT:  # not finished yet
+                    continue
+                status = "ok" if st == 0 else wost.STATUS_NAMES[st]  # BUDGET: shed; CANCELLED
                 m, se, wd, pr = wost.wost_poll(h, rq["n_points"])
                 wost.wost_solve_destroy(h)
                 with lock:
@@ -597,8 +594,12 @@ def sub_serve(wost, torch, args):
                     done.append({"latency": pr["elapsed_seconds"], "status": status, "n": rq["n_points"],
                                  "walks": int(wd.min()), "se_max": float(se.max()), "target": rq["target_se"],
                                  "steps": pr["total_steps"]})
-            time.sleep(0.002)
+            time.sleep(0.01)
 
+    # the submitting thread must not wait long for the interpreter lock
+    # while the collector sweeps thousands of live requests
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(5e-4)
     th = threading.Thread(target=collector, daemon=True)
     th.start()
     start = time.perf_counter()
@@ -628,6 +629,7 @@ def sub_serve(wost, torch, args):
         _log(f"serve: drained, {len(done)} finished, {len(live)} cancelled")
     stop.set()
     th.join(timeout=120)
+    sys.setswitchinterval(switch)
     _log("serve: collector joined")
     stats = wost.wost_engine_get_stats(eng)
     wost.wost_engine_destroy(eng)

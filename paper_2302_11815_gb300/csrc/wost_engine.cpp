@@ -46,7 +46,7 @@ struct Request {
     int stage_begin = 0, stage_end = 0;  // walks per point of the current stage
     int64_t cursor = 0;                  // next point of the stage to issue
     int outstanding = 0;                 // pieces in flight
-    double mean_steps = 64.0;            // running estimate of steps per walk
+    double mean_steps = 64.0;            // running estimate of steps per walk (from its scene's at admission)
     bool admitted = false, finished = false, started = false;
 };
 
@@ -145,6 +145,10 @@ struct wost_engine {
     std::thread th;
     CheckSet checks[kChecks];
     std::deque<int> check_order;  // busy check sets, oldest first
+    // steps per walk measured on each scene (moving average over stage
+    // checks): a new request's cost estimate, so that rounds hold the walk
+    // steps their budget pays for from the first stage on
+    std::unordered_map<const wost_scene *, double> scene_steps;
 };
 
 namespace {
@@ -200,6 +204,8 @@ void admit(wost_engine *e) {
             continue;
         }
         r->h->t_launch = Clock::now();
+        auto known = e->scene_steps.find(r->scene);
+        if (known != e->scene_steps.end()) r->mean_steps = known->second;
         r->admitted = true;
         e->used += r->bytes;
         e->st.admitted++;
@@ -226,7 +232,11 @@ void apply_check(wost_engine *e, CheckSet &cs, cudaError_t err) {
         }
         float mv;
         std::memcpy(&mv, &hv[i], 4);
-        if (hw[i]) r->mean_steps = std::max(1.0, (double)hs[i] / (double)hw[i]);
+        if (hw[i]) {
+            r->mean_steps = std::max(1.0, (double)hs[i] / (double)hw[i]);
+            auto ins = e->scene_steps.emplace(r->scene, r->mean_steps);
+            if (!ins.second) ins.first->second = 0.75 * ins.first->second + 0.25 * r->mean_steps;
+        }
         int W = r->stage_end;
         double t2 = r->target * r->target;
         bool met = r->target > 0 && (double)mv <= t2 * W;
@@ -424,6 +434,27 @@ cudaError_t ensure_graph(wost_engine *e, Slot &sl, const size_t cnt[2], const in
     return cudaGraphInstantiate(&sl.exec, sl.graph, 0);
 }
 
+// Overload shedding: requests that waited too long for their first walks,
+// admitted or still queued for memory, finish with BUDGET (checked on every
+// pass of the scheduler, not only when a round slot is free).
+void shed_late(wost_engine *e) {
+    if (e->max_wait <= 0) return;
+    std::vector<Request *> late;
+    for (Request *r : e->active)
+        if (!r->finished && !r->started && r->outstanding == 0 && since(r->t_submit) > e->max_wait)
+            late.push_back(r);
+    std::deque<Request *> keep;
+    for (Request *r : e->pending) {
+        if (!r->finished && since(r->t_submit) > e->max_wait) late.push_back(r);
+        else keep.push_back(r);
+    }
+    e->pending.swap(keep);
+    for (Request *r : late) {
+        e->st.rejected++;
+        finish(e, r, WOST_ERR_BUDGET);
+    }
+}
+
 bool launch_round(wost_engine *e) {
     int si = -1;
     for (int i = 0; i < kSlots; ++i)
@@ -432,21 +463,6 @@ bool launch_round(wost_engine *e) {
             break;
         }
     if (si < 0) return false;
-    // overload shedding: requests that waited too long for their first
-    // walks, admitted or still queued for memory
-    if (e->max_wait > 0) {
-        std::vector<Request *> late;
-        for (Request *r : e->active)
-            if (!r->finished && !r->started && r->outstanding == 0 && since(r->t_submit) > e->max_wait)
-                late.push_back(r);
-        for (Request *r : e->pending)
-            if (!r->finished && since(r->t_submit) > e->max_wait) late.push_back(r);
-        for (Request *r : late) {
-            e->st.rejected++;
-            e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), r), e->pending.end());
-            finish(e, r, WOST_ERR_BUDGET);
-        }
-    }
     // active requests with work left in their current stage, least
     // remaining stage work first (admission order among equals): under
     // overload the cheapest finish and the rest wait, instead of every
@@ -545,7 +561,10 @@ void engine_loop(wost_engine *e) {
         complete_checks(e, false);
         process_cancels(e);
         if (e->stop && e->inflight.empty() && e->check_order.empty()) break;
-        if (!e->stop) admit(e);
+        if (!e->stop) {
+            admit(e);
+            shed_late(e);
+        }
         if (!e->stop && (int)e->inflight.size() < kSlots && launch_round(e)) continue;
         // nothing to launch: wake on a submission or cancellation, or poll
         // the rounds in flight again after a short sleep

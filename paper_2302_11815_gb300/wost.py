@@ -424,6 +424,12 @@ def wost_wait(solve, timeout_s=-1.0):
     _check(load().wost_wait(solve, float(timeout_s)))
 
 
+def wost_wait_status(solve, timeout_s=0.0):
+    """wost_wait's status code, without raising (OK, TIMEOUT while it runs,
+    CANCELLED, BUDGET, ...): a cheap completion check for many requests."""
+    return int(load().wost_wait(solve, float(timeout_s)))
+
+
 def wost_cancel(solve):
     _check(load().wost_cancel(solve))
 
