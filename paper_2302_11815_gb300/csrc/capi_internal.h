@@ -6,6 +6,7 @@
 
 #include <chrono>
 #include <memory>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -41,9 +42,10 @@ struct DevBuf {
     }
     // stream-ordered allocation / release: neither waits for the device,
     // unlike cudaMalloc / cudaFree, which synchronise with all work in flight
-    cudaError_t alloc_async(size_t n, cudaStream_t s) {
+    cudaError_t alloc_async(size_t n, cudaStream_t s, cudaMemPool_t pool = nullptr) {
         bytes = n;
-        return n ? cudaMallocAsync(&p, n, s) : cudaSuccess;
+        if (!n) return cudaSuccess;
+        return pool ? cudaMallocFromPoolAsync(&p, n, pool, s) : cudaMallocAsync(&p, n, s);
     }
     void release_async(cudaStream_t s) {
         if (p) cudaFreeAsync(p, s);
@@ -113,6 +115,7 @@ struct wost_solve_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t poll_stream = nullptr;
+    bool own_poll_stream = true;  // engine requests share the engine's poll streams
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     bool own_events = false;
     std::shared_ptr<wost::BatchShared> batch;  // set for solves started by wost_solve_batch
@@ -137,6 +140,11 @@ struct wost_solve_handle {
     // host), so that destroying a request never waits for the device, whose
     // queue the engine keeps full
     bool engine_buffers = false;
+    cudaMemPool_t pool = nullptr;  // the engine's memory pool (engine requests)
+    // engine requests: set once a round holding some of the request's walks
+    // has completed; until then a poll reports no walks without reading
+    // the device (its buffers may still be being set up)
+    std::atomic<bool> engine_ready{false};
     std::chrono::steady_clock::time_point t_launch;
     double elapsed_done = -1;
     bool done = false;
@@ -154,7 +162,7 @@ struct wost_solve_handle {
         } else if (cancel_host) {
             cudaFreeHost(cancel_host);
         }
-        if (poll_stream) cudaStreamDestroy(poll_stream);
+        if (poll_stream && own_poll_stream) cudaStreamDestroy(poll_stream);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -163,8 +171,14 @@ namespace wost {
 // Layout fields of a scene's info for `lanes` lanes per walk.
 void set_layout_info(wost_scene *s, int lanes);
 // Validates a solve description, allocates and fills the solve's device
-// buffers on `stream`, fills h->sp and h->acc.  Does not launch.
-wost_status prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream, wost_solve_handle *h);
+// buffers on `stream`, fills h->sp and h->acc.  Does not launch.  With
+// fill false the buffers are only allocated: the caller uploads the points,
+// normals and flags and clears the accumulators (the serving engine does
+// both on streams of its own).
+wost_status prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream, wost_solve_handle *h,
+                          bool fill = true);
+// Zeroes a solve's accumulators and counters on `stream`.
+cudaError_t clear_accumulators(wost_solve_handle *h, cudaStream_t stream);
 // Blocks until the work queued so far on `stream` (the input copies) is done.
 wost_status wait_for_copies(cudaStream_t stream);
 // Engine side of wost_solve_destroy / wost_cancel for engine requests.

@@ -236,8 +236,17 @@ void wost::set_layout_info(wost_scene *s, int lanes) {
 
 // Validates a solve description, allocates and fills the solve's device
 // buffers on `stream`, and fills h->sp / h->acc.  Does not launch.
+cudaError_t wost::clear_accumulators(wost_solve_handle *h, cudaStream_t stream) {
+    const size_t n = (size_t)h->n_points;
+    cudaError_t e = cudaSuccess;
+    for (DevBuf *b : {&h->sum, &h->sumsq, &h->walks_done, &h->steps})
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, n * 8, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->globals.p, 0, 4 * 8, stream);
+    return e;
+}
+
 wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cudaStream_t stream,
-                                 wost_solve_handle *h) {
+                                 wost_solve_handle *h, bool fill) {
     if (!scene || !d) return fail(WOST_ERR_INVALID_ARG, "null argument");
     if (d->n_points < 1 || !d->points) return fail(WOST_ERR_INVALID_ARG, "points missing");
     if (d->n_points > 0xFFFFFFFFll) return fail(WOST_ERR_INVALID_ARG, "more than 2^32-1 points");
@@ -281,29 +290,32 @@ wost_status wost::prepare_solve(wost_scene *scene, const wost_solve_desc *d, cud
     h->lanes = lanes;
     h->stream = stream;
     const int dim = h->dim;
-    CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (!h->poll_stream) {  // (the serving engine assigns one of its own)
+        CK(cudaStreamCreateWithFlags(&h->poll_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        h->own_poll_stream = true;
+    }
     const size_t n = (size_t)d->n_points;
     // engine requests allocate on the engine's stream without waiting for it
-    auto alloc = [&](DevBuf &b, size_t bytes) { return h->engine_buffers ? b.alloc_async(bytes, stream) : b.alloc(bytes); };
+    auto alloc = [&](DevBuf &b, size_t bytes) {
+        return h->engine_buffers ? b.alloc_async(bytes, stream, h->pool) : b.alloc(bytes);
+    };
     CK(alloc(h->points, n * dim * sizeof(float)), "cudaMalloc points");
     cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, stream), "copy points");
+    if (fill) CK(cudaMemcpyAsync(h->points.p, d->points, n * dim * sizeof(float), kind, stream), "copy points");
     if (d->normals && d->on_neumann) {
         CK(alloc(h->normals, n * dim * sizeof(float)), "cudaMalloc normals");
         CK(alloc(h->onN, n), "cudaMalloc on_neumann");
-        CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, stream), "copy normals");
-        CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, stream), "copy on_neumann");
+        if (fill) {
+            CK(cudaMemcpyAsync(h->normals.p, d->normals, n * dim * sizeof(float), kind, stream), "copy normals");
+            CK(cudaMemcpyAsync(h->onN.p, d->on_neumann, n, kind, stream), "copy on_neumann");
+        }
     }
     CK(alloc(h->sum, n * 8), "cudaMalloc accumulators");
     CK(alloc(h->sumsq, n * 8), "cudaMalloc accumulators");
     CK(alloc(h->walks_done, n * 8), "cudaMalloc accumulators");
     CK(alloc(h->steps, n * 8), "cudaMalloc accumulators");
     CK(alloc(h->globals, 4 * 8), "cudaMalloc accumulators");
-    CK(cudaMemsetAsync(h->sum.p, 0, n * 8, stream), "memset");
-    CK(cudaMemsetAsync(h->sumsq.p, 0, n * 8, stream), "memset");
-    CK(cudaMemsetAsync(h->walks_done.p, 0, n * 8, stream), "memset");
-    CK(cudaMemsetAsync(h->steps.p, 0, n * 8, stream), "memset");
-    CK(cudaMemsetAsync(h->globals.p, 0, 4 * 8, stream), "memset");
+    if (fill) CK(clear_accumulators(h, stream), "memset");
     if (!h->cancel_host) {
         CK(cudaHostAlloc((void **)&h->cancel_host, sizeof(int), cudaHostAllocMapped), "cudaHostAlloc");
         *h->cancel_host = 0;
@@ -571,7 +583,9 @@ wost_status wost_poll(wost_solve_handle *h, double *mean, double *se, uint64_t *
         if (st != WOST_OK) return st;
         bool was_done = h->done;
         const size_t n = (size_t)h->n_points;
-        if (!h->sum.p) {  // an engine request not admitted yet: nothing accumulated
+        // an engine request not admitted yet, or none of whose rounds has
+        // completed: nothing accumulated
+        if (!h->sum.p || (h->engine_buffers && !h->engine_ready.load())) {
             for (size_t i = 0; i < n; ++i) {
                 if (mean) mean[i] = 0;
                 if (se) se[i] = 0;

@@ -119,20 +119,44 @@ struct CheckSet {
 };
 
 constexpr int kChecks = 4;  // stage checks in flight at most
+constexpr int kStage = 8;                  // pinned staging slots for request inputs
+constexpr int kPollStreams = 8;            // poll streams shared by the engine's requests
+constexpr size_t kStageBytes = 8u << 20;   // bytes per slot
 
 }  // namespace
 
 struct wost_engine {
     int device = 0;
     cudaStream_t stream = nullptr, check_stream = nullptr;  // admissions; stage checks
-    cudaEvent_t ev_admit = nullptr;                   // orders a request's poll stream after its set-up
     cudaEvent_t ev_ready = nullptr;                   // orders a round after the admissions before it
+    cudaStream_t copy_stream = nullptr;               // submissions' copies of device inputs
+    // requests poll on these (creating a stream per request waits for the
+    // device: measured up to 2 s with rounds resident)
+    cudaStream_t poll[kPollStreams] = {};
+    int poll_next = 0;
+    // request buffers come from the engine's own pool, which keeps what is
+    // freed (no trimming, so no remapping on later allocations)
+    cudaMemPool_t pool = nullptr;
+    // admissions: allocations and input uploads on `stream` (copies only, no
+    // kernels, so they complete while rounds fill the SMs), the zeroing of
+    // the accumulators on `zero_stream` (high priority); rounds wait for both
+    cudaStream_t zero_stream = nullptr;
+    cudaEvent_t ev_alloc = nullptr;
+    cudaEvent_t ev_detach = nullptr;  // orders a released request's frees after its set-up
+    // pinned staging slots the inputs are uploaded from (a copy from
+    // pageable memory is synchronous and may wait on the device); a slot is
+    // free again once its event has completed, and an admission that finds
+    // none free waits for a later pass of the scheduler
+    unsigned char *stage = nullptr;
+    cudaEvent_t stage_ev[kStage] = {};
+    bool stage_busy[kStage] = {};
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
     double min_round_steps = 1e5;     // keeps the resident grid supplied with walks
     int min_walks = 16, cap = 65536, block = 128;
     std::mutex mu;
+    std::mutex copy_mu;  // the copy stream (submissions from several threads)
     std::condition_variable cv, done_cv;
     std::deque<Request *> pending;
     std::vector<Request *> active;
@@ -172,6 +196,60 @@ void finish(wost_engine *e, Request *r, wost_status status) {
 
 bool cancelled(const Request *r) { return *(volatile int *)r->h->cancel_host != 0; }
 
+// A free staging slot (-1: none now).
+int free_stage(wost_engine *e) {
+    for (int i = 0; i < kStage; ++i) {
+        if (e->stage_busy[i] && cudaEventQuery(e->stage_ev[i]) != cudaErrorNotReady) e->stage_busy[i] = false;
+        if (!e->stage_busy[i]) return i;
+    }
+    return -1;
+}
+
+// Allocates a request's buffers, uploads its inputs from a staging slot
+// (or, for inputs larger than a slot, straight from its host copy) and
+// clears its accumulators.  Polls read the buffers only once a round with
+// the request's walks has completed, and rounds run after all of this.
+wost_status set_up(wost_engine *e, Request *r, int slot) {
+    r->h->poll_stream = e->poll[e->poll_next];
+    r->h->own_poll_stream = false;
+    e->poll_next = (e->poll_next + 1) % kPollStreams;
+    wost_status s = prepare_solve(r->scene, &r->desc, e->stream, r->h, false);
+    r->h->stream = nullptr;  // the engine's streams are not the handle's to synchronize
+    if (s != WOST_OK) return s;
+    wost_solve_handle *h = r->h;
+    const size_t n = (size_t)h->n_points, pb = n * h->dim * sizeof(float);
+    const bool has_n = !r->nrm.empty();
+    cudaError_t er = cudaSuccess;
+    auto put = [&](void *dst, const void *src, size_t bytes, size_t &off) {
+        if (er != cudaSuccess) return;
+        if (slot >= 0) {
+            unsigned char *buf = e->stage + (size_t)slot * kStageBytes + off;
+            std::memcpy(buf, src, bytes);
+            er = cudaMemcpyAsync(dst, buf, bytes, cudaMemcpyHostToDevice, e->stream);
+            off += (bytes + 15) & ~(size_t)15;
+        } else {
+            er = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, e->stream);
+        }
+    };
+    size_t off = 0;
+    put(h->points.p, r->pts.data(), pb, off);
+    if (has_n) {
+        put(h->normals.p, r->nrm.data(), pb, off);
+        put(h->onN.p, r->onN.data(), n, off);
+    }
+    if (er == cudaSuccess && slot >= 0 && (er = cudaEventRecord(e->stage_ev[slot], e->stream)) == cudaSuccess)
+        e->stage_busy[slot] = true;
+    if (er == cudaSuccess) er = cudaEventRecord(e->ev_alloc, e->stream);
+    if (er == cudaSuccess) er = cudaStreamWaitEvent(e->zero_stream, e->ev_alloc, 0);
+    if (er == cudaSuccess) er = clear_accumulators(h, e->zero_stream);
+    return er == cudaSuccess ? WOST_OK : fail(WOST_ERR_CUDA, "setting up a request");
+}
+
+size_t input_bytes(const Request *r) {
+    const size_t b = r->pts.size() * sizeof(float) + r->nrm.size() * sizeof(float) + r->onN.size();
+    return b + 32;  // alignment of the second and third arrays
+}
+
 void admit(wost_engine *e) {
     while (!e->pending.empty()) {
         Request *r = e->pending.front();
@@ -181,17 +259,13 @@ void admit(wost_engine *e) {
             continue;
         }
         if (e->used + r->bytes > e->budget) break;  // FIFO: later requests wait too
+        int slot = -1;
+        if (input_bytes(r) <= kStageBytes && (slot = free_stage(e)) < 0) break;  // no slot free yet
         e->pending.pop_front();
         wost_status s;
         {
             std::lock_guard<std::mutex> hl(r->h->mu);  // pollers see either nothing or a complete state
-            s = prepare_solve(r->scene, &r->desc, e->stream, r->h);
-            r->h->stream = nullptr;  // the engine's stream is not the handle's to synchronize
-            // the buffers were allocated and cleared on the engine's stream:
-            // the handle's poll stream reads them only after that
-            if (s == WOST_OK && (cudaEventRecord(e->ev_admit, e->stream) != cudaSuccess ||
-                                 cudaStreamWaitEvent(r->h->poll_stream, e->ev_admit, 0) != cudaSuccess))
-                s = fail(WOST_ERR_CUDA, "ordering the poll stream after admission");
+            s = set_up(e, r, slot);
         }
         r->pts.clear();
         r->pts.shrink_to_fit();
@@ -298,8 +372,8 @@ void issue_check(wost_engine *e, std::vector<Request *> &ready) {
         cs.out.release_async(e->check_stream);
         if ((err = cudaMallocHost((void **)&cs.host_jobs, nc * sizeof(StatJob))) == cudaSuccess &&
             (err = cudaMallocHost((void **)&cs.host_out, nc * 32)) == cudaSuccess &&
-            (err = cs.jobs.alloc_async(nc * sizeof(StatJob), e->check_stream)) == cudaSuccess &&
-            (err = cs.out.alloc_async(nc * 32, e->check_stream)) == cudaSuccess)
+            (err = cs.jobs.alloc_async(nc * sizeof(StatJob), e->check_stream, e->pool)) == cudaSuccess &&
+            (err = cs.out.alloc_async(nc * 32, e->check_stream, e->pool)) == cudaSuccess)
             cs.cap = nc;
     }
     if (err == cudaSuccess && !cs.ev) err = cudaEventCreateWithFlags(&cs.ev, cudaEventDisableTiming);
@@ -352,6 +426,7 @@ void retire(wost_engine *e, size_t i) {
     std::vector<Request *> ready;
     e->done_cv.notify_all();
     for (auto &p : rd.pieces) {
+        p.r->h->engine_ready.store(true);
         p.r->outstanding--;
         if (!p.r->finished && p.r->outstanding == 0 && p.r->cursor >= p.r->h->n_points &&
             std::find(ready.begin(), ready.end(), p.r) == ready.end())
@@ -532,8 +607,10 @@ bool launch_round(wost_engine *e) {
         BatchHeader hd{(int)cnt[di], 0, total[di]};
         std::memcpy(sl.host[di], &hd, sizeof hd);
     }
-    // the round runs after the admissions (buffer set-up) issued before it
+    // the round runs after the admissions (uploads, zeroing) issued before it
     err = cudaEventRecord(e->ev_ready, e->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sl.stream, e->ev_ready, 0);
+    if (err == cudaSuccess) err = cudaEventRecord(e->ev_ready, e->zero_stream);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(sl.stream, e->ev_ready, 0);
     if (err == cudaSuccess) err = cudaEventRecord(sl.ev0, sl.stream);
     if (err == cudaSuccess) err = cudaGraphLaunch(sl.exec, sl.stream);
@@ -594,6 +671,12 @@ void engine_detach(wost_engine *e, wost_solve_handle *h) {
         e->cv.notify_all();
     }
     e->done_cv.wait(lk, [&] { return r->finished && r->outstanding == 0; });
+    // a request none of whose rounds ran may still have its set-up queued:
+    // its buffers are freed on its poll stream after that work
+    if (r->admitted && !h->engine_ready.load()) {
+        for (cudaStream_t st : {e->stream, e->zero_stream})
+            if (cudaEventRecord(e->ev_detach, st) == cudaSuccess) cudaStreamWaitEvent(h->poll_stream, e->ev_detach, 0);
+    }
     if (r->admitted) e->used -= r->bytes;
     e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), r), e->pending.end());
     e->by_handle.erase(it);
@@ -639,8 +722,23 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
         CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
         CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
         CK(cudaStreamCreateWithPriority(&e->check_stream, cudaStreamNonBlocking, prio_high), "cudaStreamCreate");
-        CK(cudaEventCreateWithFlags(&e->ev_admit, cudaEventDisableTiming), "cudaEventCreate");
         CK(cudaEventCreateWithFlags(&e->ev_ready, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaStreamCreateWithFlags(&e->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (auto &ps : e->poll) CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking), "cudaStreamCreate");
+        {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = d->device;
+            CK(cudaMemPoolCreate(&e->pool, &props), "cudaMemPoolCreate");
+            uint64_t keep_all = ~0ull;
+            CK(cudaMemPoolSetAttribute(e->pool, cudaMemPoolAttrReleaseThreshold, &keep_all), "cudaMemPoolSetAttribute");
+        }
+        CK(cudaMallocHost((void **)&e->stage, kStage * kStageBytes), "cudaMallocHost");
+        for (auto &ev : e->stage_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_alloc, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventCreateWithFlags(&e->ev_detach, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaStreamCreateWithPriority(&e->zero_stream, cudaStreamNonBlocking, prio_high), "cudaStreamCreate");
         for (auto &s : e->slots) {
             CK(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "cudaStreamCreate");
             CK(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -689,14 +787,25 @@ wost_status wost_engine_submit(wost_engine *e, wost_scene *scene, const wost_sol
             return fail(WOST_ERR_BUDGET, "request exceeds the engine's memory budget");
         }
         CK(cudaSetDevice(e->device), "cudaSetDevice");
+        // the inputs are copied before return: host arrays with memcpy (a
+        // CUDA host-to-host copy goes through the legacy stream and may wait
+        // on the device), device arrays on the engine's copy stream
+        auto copy_in = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+            if (d->memory == WOST_MEM_HOST) {
+                std::memcpy(dst, src, bytes);
+                return cudaSuccess;
+            }
+            std::lock_guard<std::mutex> ck(e->copy_mu);
+            cudaError_t er = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, e->copy_stream);
+            return er == cudaSuccess ? cudaStreamSynchronize(e->copy_stream) : er;
+        };
         r->pts.resize(n * dim);
-        cudaMemcpyKind kind = d->memory == WOST_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
-        CK(cudaMemcpy(r->pts.data(), d->points, n * dim * 4, kind), "copy points");
+        CK(copy_in(r->pts.data(), d->points, n * dim * 4), "copy points");
         if (has_n) {
             r->nrm.resize(n * dim);
             r->onN.resize(n);
-            CK(cudaMemcpy(r->nrm.data(), d->normals, n * dim * 4, kind), "copy normals");
-            CK(cudaMemcpy(r->onN.data(), d->on_neumann, n, kind), "copy on_neumann");
+            CK(copy_in(r->nrm.data(), d->normals, n * dim * 4), "copy normals");
+            CK(copy_in(r->onN.data(), d->on_neumann, n), "copy on_neumann");
         }
         r->desc = *d;
         r->desc.points = r->pts.data();
@@ -719,6 +828,7 @@ wost_status wost_engine_submit(wost_engine *e, wost_scene *scene, const wost_sol
         // request's pieces), so it is plain host memory, and the request's
         // device buffers are stream-ordered (no device-wide wait on destroy)
         h->engine_buffers = true;
+        h->pool = e->pool;
         h->cancel_host = new int(0);
         h->cancel_dev = nullptr;
         r->h = h.get();
@@ -768,15 +878,36 @@ wost_status wost_engine_destroy(wost_engine *e) {
         if (s.stream) cudaStreamSynchronize(s.stream);
     for (auto &kv : e->by_handle) {
         kv.first->engine = nullptr;  // the handle outlives the engine
+        if (!kv.first->own_poll_stream) {  // and needs a poll stream of its own
+            std::lock_guard<std::mutex> hl(kv.first->mu);
+            if (cudaStreamCreateWithFlags(&kv.first->poll_stream, cudaStreamNonBlocking) != cudaSuccess)
+                kv.first->poll_stream = nullptr;
+            kv.first->own_poll_stream = true;
+        }
         delete kv.second;
     }
     e->by_handle.clear();
     cudaStreamSynchronize(e->check_stream);
     cudaStreamDestroy(e->check_stream);
-    cudaEventDestroy(e->ev_admit);
     cudaEventDestroy(e->ev_ready);
+    cudaStreamSynchronize(e->zero_stream);
+    for (cudaEvent_t ev : e->stage_ev)
+        if (ev) cudaEventDestroy(ev);
+    cudaEventDestroy(e->ev_alloc);
+    cudaEventDestroy(e->ev_detach);
+    if (e->stage) cudaFreeHost(e->stage);
+    cudaStreamDestroy(e->zero_stream);
+    cudaStreamDestroy(e->copy_stream);
+    for (cudaStream_t ps : e->poll) {
+        cudaStreamSynchronize(ps);
+        cudaStreamDestroy(ps);
+    }
     cudaStreamDestroy(e->stream);
+    cudaMemPool_t pool = e->pool;
     delete e;  // the slots release their graphs, streams and events
+    // a pool with allocations outstanding (handles that outlive the engine)
+    // is released once they are freed
+    if (pool) cudaMemPoolDestroy(pool);
     return WOST_OK;
 }
 
