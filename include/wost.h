@@ -413,9 +413,10 @@ wost_status wost_engine_create(const wost_engine_desc *desc, wost_engine **out);
  * desc->walks_per_point is the request's walk cap (0 or larger than the
  * engine's cap: the engine's cap).  target_se > 0: stop once every point's
  * standard error is <= target_se; target_se == 0: run exactly the cap.
- * Inputs are copied before return.  The handle works with wost_poll,
- * wost_wait (CANCELLED for a cancelled request), wost_cancel and
- * wost_solve_destroy.  Errors: INVALID_ARG; BUDGET if the request alone
+ * Inputs are copied before return.  The handle works with wost_poll
+ * (no walks reported until a round holding some of the request's walks has
+ * completed), wost_wait (CANCELLED for a cancelled request; BUDGET for one
+ * shed by the wait limit), wost_cancel and wost_solve_destroy.  Errors: INVALID_ARG; BUDGET if the request alone
  * exceeds the memory budget (it could never be admitted). */
 wost_status wost_engine_submit(wost_engine *engine, wost_scene *scene, const wost_solve_desc *desc,
                                double target_se, wost_solve_handle **out);
