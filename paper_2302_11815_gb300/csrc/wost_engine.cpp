@@ -153,7 +153,11 @@ struct wost_engine {
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
-    double min_round_steps = 1e5;     // keeps the resident grid supplied with walks
+    // a round gives every resident lane of its grid this many walks of 64
+    // steps at least, else its time is that of its longest walk with the
+    // grid mostly idle; the grid depends on the traversal stack depth
+    // (shared memory per block), so the lanes are looked up per depth
+    std::unordered_map<int, double> lanes_at_depth[2];
     int min_walks = 16, cap = 65536, block = 128;
     std::mutex mu;
     std::mutex copy_mu;  // the copy stream (submissions from several threads)
@@ -530,6 +534,34 @@ void shed_late(wost_engine *e) {
     }
 }
 
+#ifndef WOST_ROUND_WALKS
+#define WOST_ROUND_WALKS 4
+#endif
+
+// Resident lanes of the batched kernel for a dimension at a stack depth.
+double lanes_at(wost_engine *e, int dim, int depth) {
+    auto &m = e->lanes_at_depth[dim - 2];
+    auto it = m.find(depth);
+    if (it != m.end()) return it->second;
+    int blocks = 0;
+    double lanes = batch_grid(dim, e->block, std::max(depth, 2), &blocks) == cudaSuccess ? (double)blocks * e->block
+                                                                                           : 0.0;
+    m[depth] = lanes;
+    return lanes;
+}
+
+// The round's walk-step floor: WOST_ROUND_WALKS walks of 64 steps for every
+// resident lane (the deepest stack of each dimension sets that dimension's
+// grid; 2D and 3D kernels share the SMs, so the larger grid counts).
+double min_round_steps(wost_engine *e, const std::vector<Request *> &iss) {
+    int depth[2] = {0, 0};
+    for (const Request *r : iss) depth[r->h->dim - 2] = std::max(depth[r->h->dim - 2], r->scene->stack_depth);
+    double lanes = 0;
+    for (int di = 0; di < 2; ++di)
+        if (depth[di]) lanes = std::max(lanes, lanes_at(e, di + 2, depth[di]));
+    return (double)WOST_ROUND_WALKS * 64.0 * lanes;
+}
+
 bool launch_round(wost_engine *e) {
     int si = -1;
     for (int i = 0; i < kSlots; ++i)
@@ -556,7 +588,7 @@ bool launch_round(wost_engine *e) {
     // the round's budget goes down that order: each request takes as many
     // points of its current stage as the remaining budget pays for (at
     // least one point, so every round makes progress)
-    double remaining = std::max(e->round_budget_steps, e->min_round_steps);
+    double remaining = std::max(e->round_budget_steps, min_round_steps(e, iss));
     for (Request *r : iss) {
         if (remaining <= 0) break;
         int64_t left = r->h->n_points - r->cursor;
@@ -711,13 +743,6 @@ wost_status wost_engine_create(const wost_engine_desc *d, wost_engine **out) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
         e->budget = d->memory_budget_bytes ? d->memory_budget_bytes : (int64_t)(fr / 4);
-        {
-            // a round must give every resident lane several walks, else its
-            // time is that of its longest walk with the grid mostly idle
-            int blocks3 = 0;
-            CK(batch_grid(3, block, 64, &blocks3), "occupancy");
-            e->min_round_steps = 4.0 * 64.0 * (double)blocks3 * block;
-        }
         int prio_low = 0, prio_high = 0;
         CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "cudaDeviceGetStreamPriorityRange");
         CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking), "cudaStreamCreate");
