@@ -144,6 +144,34 @@ def test_engine_target_and_cap(wost, mix):
     np.testing.assert_allclose(m, ref["mean"], **FP32_WALKS)
 
 
+def test_engine_device_inputs_and_early_poll(wost, mix):
+    """A request whose points are device memory (copied on the engine's own
+    stream at submission) gives the walks of the same request from host
+    memory; a poll right after submission reports no walks rather than
+    reading buffers still being set up."""
+    specs, S = mix
+    sc = specs[1]
+    eng = wost.wost_engine_create()
+    hs = []
+    try:
+        for pts in (sc["points"], torch.from_numpy(sc["points"]).cuda()):
+            h = wost.wost_engine_submit(eng, S[1].handle, pts, 0.0, 24, sc["epsilon"], sc["r_min"],
+                                        sc["max_steps"], seed=77)
+            hs.append(h)
+            m0, se0, w0, pr0 = wost.wost_poll(h, len(sc["points"]))
+            assert int(w0.sum()) == pr0["walks_done"] and pr0["walks_done"] <= len(sc["points"]) * 24
+        for h in hs:
+            wost.wost_wait(h, 300)
+        res = [wost.wost_poll(h, len(sc["points"])) for h in hs]
+    finally:
+        for h in hs:
+            wost.wost_solve_destroy(h)
+        wost.wost_engine_destroy(eng)
+    assert np.all(res[0][2] == 24) and np.all(res[1][2] == 24)
+    np.testing.assert_allclose(res[1][0], res[0][0], **FP32_WALKS)
+    assert res[1][3]["total_steps"] == res[0][3]["total_steps"]
+
+
 def test_engine_budget_admission_and_rejection(wost, mix):
     specs, S = mix
     sc = specs[0]
