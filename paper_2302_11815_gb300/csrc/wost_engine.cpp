@@ -5,7 +5,8 @@
 // persistent launch (k_walk_batch, one per dimension present) over "pieces"
 // -- point ranges x walk ranges -- of every active request, sized so that a
 // round takes about round_seconds of GPU time (the walk-step budget adapts to
-// the measured round times).  Every round slot has streams of its own and up
+// the measured round times), but never less than a few walks per resident
+// lane (min_round_steps).  Every round slot has streams of its own and up
 // to three rounds are in flight: a round lasts until its longest walk ends,
 // and the next rounds' blocks take the SMs that its finished blocks free, so
 // the tail of one round overlaps the bulk of the next and the host prepares
@@ -153,10 +154,9 @@ struct wost_engine {
     int64_t budget = 0, used = 0;
     double round_seconds = 0.02;
     double max_wait = 0;              // seconds a request may wait for its first walks (0: no limit)
-    // a round gives every resident lane of its grid this many walks of 64
-    // steps at least, else its time is that of its longest walk with the
-    // grid mostly idle; the grid depends on the traversal stack depth
-    // (shared memory per block), so the lanes are looked up per depth
+    // resident lanes of the batched kernel per traversal stack depth (the
+    // shared memory per block sets the grid), for the rounds' walk-step
+    // floor (min_round_steps)
     std::unordered_map<int, double> lanes_at_depth[2];
     int min_walks = 16, cap = 65536, block = 128;
     std::mutex mu;
