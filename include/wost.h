@@ -370,8 +370,9 @@ wost_status wost_solve_static(wost_scene *scene, int64_t n_points, const float *
  * short of walks; the round's walk-step budget goes to the active requests
  * with the least work left in their current stage first, so under overload
  * the cheapest complete and the rest wait (or are shed by
- * max_wait_seconds).  Up to two rounds are queued so
- * the GPU never waits for the host.  A request runs in stages of walks per point
+ * max_wait_seconds).  Up to three rounds run concurrently (each on streams
+ * of its own, so one round's last walks overlap the next rounds), and the
+ * GPU never waits for the host.  A request runs in stages of walks per point
  * (min_walks, then growing from its own variance estimate); after each
  * stage it completes if its largest per-point standard error is at most its
  * target, or if it reached its walk cap.  A request's walks use its own
