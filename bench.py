@@ -517,13 +517,33 @@ def sub_batch(wost, torch, args):
         u = scenes.exact_u(*sc["exact"], sc["points"])
         err2 += float(np.sum((r[0] - u) ** 2))
         ref2 += float(np.sum(u**2))
+    # roofline of the batched launches: each scene's algorithmic bytes per
+    # walk step from the counting kernel on 2 of its walks per point (the
+    # binary-tree records: 48-byte nodes in 2D, 64 in 3D, 32-byte cones)
+    # times the walk steps the scene ran in the batch, over the batch time
+    alg = 0.0
+    for s, sc, p, r in zip(S, specs, pts, rb):
+        rc = wost.solve(s, p, min(2, sc["walks"]), sc["epsilon"], sc["r_min"], sc["max_steps"], seed=sc["seed"],
+                        kernel="counting", stream=stream)
+        if rc["total_steps"] > 0:
+            b_step, _ = work_per_step(rc["counts"], rc["total_steps"], sc["dim"],
+                                      dict(s.info(), lanes_per_walk=1, node_bytes=48 if sc["dim"] == 2 else 64,
+                                           cone_bytes=32))
+            alg += b_step * r[3]["total_steps"]
+    peaks, peak_src = _measured_peaks()
+    roof = {"bound": "hbm", "achieved": alg / tb / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": alg / tb / 1e9 / peaks["hbm_gbs"], "bytes_per_step": alg / max(steps, 1), "peak_src": peak_src,
+            "kernel": "k_walk_batch<2/3, Poisson> (2D and 3D launches, concurrent)",
+            "model": "per-scene counting-kernel bytes per walk step x the scene's walk steps in the batch"}
+    _log(f"batched roofline: {roof['achieved']:.0f} GB/s, {roof['frac']:.3f} of HBM")
     for s in S:
         s.close()
     return {"workload": f"batched_{len(specs)}_scenes", "n_scenes": len(specs),
             "scenes_2d": sum(1 for s in specs if s["dim"] == 2), "total_walks": int(walks), "total_steps": int(steps),
             "total_points": int(sum(len(s["points"]) for s in specs)),
             "total_prims": int(sum(len(s["prims"]) for s in specs)),
-            "batched": {"seconds": tb, "walk_steps_per_s": steps / tb, "launches": len({s["dim"] for s in specs})},
+            "batched": {"seconds": tb, "walk_steps_per_s": steps / tb, "launches": len({s["dim"] for s in specs}),
+                        "roofline": roof},
             "per_scene_persistent": {"seconds": tp, "walk_steps_per_s": steps / tp, "launches": len(specs)},
             "per_scene_plain": {"seconds": tq, "walk_steps_per_s": steps / tq, "launches": len(specs)},
             "speedup_vs_plain": tq / tb, "speedup_vs_per_scene_persistent": tp / tb,
