@@ -521,21 +521,32 @@ def sub_batch(wost, torch, args):
     # walk step from the counting kernel on 2 of its walks per point (the
     # binary-tree records: 48-byte nodes in 2D, 64 in 3D, 32-byte cones)
     # times the walk steps the scene ran in the batch, over the batch time
-    alg = 0.0
-    for s, sc, p, r in zip(S, specs, pts, rb):
+    b_scene = []
+    for s, sc, p in zip(S, specs, pts):
         rc = wost.solve(s, p, min(2, sc["walks"]), sc["epsilon"], sc["r_min"], sc["max_steps"], seed=sc["seed"],
                         kernel="counting", stream=stream)
-        if rc["total_steps"] > 0:
-            b_step, _ = work_per_step(rc["counts"], rc["total_steps"], sc["dim"],
-                                      dict(s.info(), lanes_per_walk=1, node_bytes=48 if sc["dim"] == 2 else 64,
-                                           cone_bytes=32))
-            alg += b_step * r[3]["total_steps"]
+        b_scene.append(work_per_step(rc["counts"], rc["total_steps"], sc["dim"],
+                                     dict(s.info(), lanes_per_walk=1, node_bytes=48 if sc["dim"] == 2 else 64,
+                                          cone_bytes=32))[0] if rc["total_steps"] > 0 else 0.0)
     peaks, peak_src = _measured_peaks()
-    roof = {"bound": "hbm", "achieved": alg / tb / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": alg / tb / 1e9 / peaks["hbm_gbs"], "bytes_per_step": alg / max(steps, 1), "peak_src": peak_src,
-            "kernel": "k_walk_batch<2/3, Poisson> (2D and 3D launches, concurrent)",
-            "model": "per-scene counting-kernel bytes per walk step x the scene's walk steps in the batch"}
+
+    def roofline(res, secs):
+        alg = sum(b * r[3]["total_steps"] for b, r in zip(b_scene, res))
+        n = sum(r[3]["total_steps"] for r in res)
+        return {"bound": "hbm", "achieved": alg / secs / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": alg / secs / 1e9 / peaks["hbm_gbs"], "bytes_per_step": alg / max(n, 1), "peak_src": peak_src,
+                "kernel": "k_walk_batch<2/3, Poisson> (2D and 3D launches, concurrent)",
+                "model": "per-scene counting-kernel bytes per walk step x the scene's walk steps in the batch"}
+
+    roof = roofline(rb, tb)
     _log(f"batched roofline: {roof['achieved']:.0f} GB/s, {roof['frac']:.3f} of HBM")
+    # the same scenes and points with 8x the walks: ~24 walks per resident
+    # lane, so the launch is no longer one wave as long as its longest walks
+    reqs = [dict(r, walks_per_point=8 * r["walks_per_point"]) for r in reqs]
+    r8, t8 = timed(batched)
+    steps8 = sum(r[3]["total_steps"] for r in r8)
+    roof8 = roofline(r8, t8)
+    _log(f"batched, 8x walks: {t8:.1f} s, {steps8 / t8:.3e} steps/s, {roof8['frac']:.3f} of HBM")
     for s in S:
         s.close()
     return {"workload": f"batched_{len(specs)}_scenes", "n_scenes": len(specs),
@@ -544,6 +555,8 @@ def sub_batch(wost, torch, args):
             "total_prims": int(sum(len(s["prims"]) for s in specs)),
             "batched": {"seconds": tb, "walk_steps_per_s": steps / tb, "launches": len({s["dim"] for s in specs}),
                         "roofline": roof},
+            "batched_8x_walks": {"seconds": t8, "total_steps": int(steps8), "walk_steps_per_s": steps8 / t8,
+                                 "walks_per_point": [128, 8 * args.batch_max_walks], "roofline": roof8},
             "per_scene_persistent": {"seconds": tp, "walk_steps_per_s": steps / tp, "launches": len(specs)},
             "per_scene_plain": {"seconds": tq, "walk_steps_per_s": steps / tq, "launches": len(specs)},
             "speedup_vs_plain": tq / tb, "speedup_vs_per_scene_persistent": tp / tb,
