@@ -705,9 +705,12 @@ def run_ours(args):
     tune = None
     if not args.block:
         # the library's autotuner picks the layout (lanes per walk) and block
-        # size on a sample of the grid; the timed launches use its choice
+        # size on a sample of the grid at the workload's walks per point
+        # (~8,200 points x 256 walks: ~13 walks per resident lane, so every
+        # lane stays busy through the timed launches); the timed launches
+        # use its choice
         sample = torch.from_numpy(grid_pts[:: max(1, len(grid_pts) // 8192)].copy()).cuda()
-        tune = wost.wost_scene_autotune(S.handle, sample, 8, sc["epsilon"], sc["r_min"], sc["max_steps"])
+        tune = wost.wost_scene_autotune(S.handle, sample, walks, sc["epsilon"], sc["r_min"], sc["max_steps"])
         _log(f"autotune: {tune['lanes_per_walk']} lane(s) per walk, block {tune['block_size']}")
     info = S.info()
     stream = torch.cuda.Stream()
