@@ -1,5 +1,6 @@
-"""Host logic of bench.py on the CPU: the clock-sample summary and the
-algorithmic work model behind the roofline figure."""
+"""Host logic of bench.py on the CPU: the clock-sample summary, the
+algorithmic work model and the arithmetic of the roofline figure, and the
+record of profiled DRAM traffic it draws on."""
 import os
 import sys
 
@@ -39,3 +40,33 @@ def test_work_model_bytes_and_flops(lanes, node_bytes, cone_bytes, children):
     expect_f = (30 * children * bench.CHILD_FLOPS[2]["q1"] + 20 * children * bench.CHILD_FLOPS[2]["q2"]
                 + 5 * bench.PRIM_FLOPS[2]["q3"]) / 10 + bench.STEP_FLOPS[2]
     assert f == pytest.approx(expect_f)
+
+
+def test_roofline_fraction_traffic_and_per_launch_bytes():
+    peaks = {"hbm_gbs": 6000.0}
+    # 3 launches of 1e9 walk steps in 2 s at 3,000 algorithmic bytes and 2,000 flops per step
+    r = bench.roofline_block("k", 3000.0, 2000.0, 3e9, 2.0, 3, peaks, "measured", 20000.0, 7000.0, 80.0, "x",
+                             0.5, {})
+    assert r["achieved"] == pytest.approx(3000.0 * 3e9 / 2.0 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0) and r["peak"] == 6000.0
+    assert r["l2_frac"] == pytest.approx(r["achieved"] / 20000.0)
+    assert r["achieved_tflops"] == pytest.approx(2000.0 * 3e9 / 2.0 / 1e12)
+    assert r["fp32_frac"] == pytest.approx(r["achieved_tflops"] / 80.0)
+    assert r["algorithmic_bytes_per_launch"] == pytest.approx(3000.0 * 1e9)
+    assert r["traffic"] == pytest.approx(0.5 * 1e9)  # DRAM bytes per step x the steps of one launch
+    assert bench.roofline_block("k", 1.0, 1.0, 1.0, 1.0, 1, peaks, "m", 1.0, 1.0, 1.0, "x", None, {})["traffic"] is None
+
+
+def test_traffic_record_format_and_lookup():
+    """Every record of profiles/traffic.txt names a kernel, a 16-digit source
+    hash and DRAM bytes per walk step; the lookup returns a record's figure
+    only for its own hash."""
+    path = os.path.join(bench.ROOT, "profiles", "traffic.txt")
+    recs = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert recs
+    for f in recs:
+        assert f[0].startswith("k_walk_") and len(f[1]) == 16 and int(f[1], 16) >= 0 and float(f[2]) >= 0
+        assert bench.profiled_traffic(f[0], f[1]) == float(f[2])
+    assert bench.profiled_traffic(recs[0][0], "0" * 16) is None
+    h = bench.kernel_source_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
