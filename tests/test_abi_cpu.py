@@ -155,6 +155,30 @@ def test_scene_hierarchies_are_well_formed(lib, name, leaf):
     assert info["n_silhouette"] >= 1 and info["depth_silhouette"] >= 1
 
 
+@pytest.mark.parametrize("name", ["slit", "crack", "sheet", "plate", "keyhole"])
+@pytest.mark.parametrize("split", [0, 1])
+def test_double_sided_and_stress_scenes_are_well_formed(lib, name, split):
+    # App. B's double-sided scenes (flags 2 and 3) and the keyhole, with the
+    # surface-area x orientation split of the silhouette tree (0) and plain
+    # SAH (1): every record counted once, double-sided records kept on their
+    # side of the Dirichlet / Neumann split, hierarchies well formed
+    from paper_2302_11815_gb300 import wost
+
+    sc = {"slit": scenes.slit_square_scene, "crack": scenes.crack_square_scene,
+          "sheet": scenes.sheet_square_scene, "plate": scenes.plate_cube_scene,
+          "keyhole": scenes.keyhole_scene}[name]()
+    sc = dict(sc, silhouette_split=split)
+    info = wost.wost_scene_validate(sc)
+    flags = np.asarray(sc["flags"])
+    assert info["n_dirichlet"] + info["n_neumann"] + info["n_dropped"] == len(sc["prims"])
+    if info["n_dropped"] == 0:
+        assert info["n_dirichlet"] == int(np.isin(flags, (0, 2)).sum())
+        assert info["n_neumann"] == int(np.isin(flags, (1, 3)).sum())
+    assert info["depth_dirichlet"] >= 1
+    if info["n_neumann"]:  # (the slit scene is all Dirichlet: no silhouette candidates)
+        assert info["n_silhouette"] >= 1 and info["depth_silhouette"] >= 1
+
+
 def test_batched_workload_scenes_are_well_formed(lib):
     # the batched workload's generator (2D radial polygons with holes, 3D
     # cube + torus), scenes capped at 20k primitives here: every scene
